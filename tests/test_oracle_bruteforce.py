@@ -1,0 +1,148 @@
+"""Brute-force pin of the oracle's whole time step on small periodic boxes.
+
+An independent, literal numpy implementation of one step of Section 3:
+
+* neighbours by ``np.roll`` (not the oracle's index arithmetic);
+* the hydrodynamic collision in moment space exactly as eq:improved_collision
+  writes it, g* = M^{-1} [m - S (m - m^eq + F_m / 2) + F_m], with M built by
+  w-weighted Gram-Schmidt of the monomials in degree order (the "weighted
+  orthogonal moment set" of Section 6.1), S = diag(1, 1, 1, 1, s_nu x 6, 1, ...),
+  F_m = rho^{-1} (0, F, 0, ...);
+* the viscous force eq:viscousForce with the collision matrix Omega = M^{-1} S M
+  applied to (g - g^eq) literally;
+* the phase-field update eq:lb_interface with Omega = omega_phi I.
+
+It shares nothing with the oracle's closed (Hermite) form of the collision, so a
+wrong coefficient, sign or index in that reduction fails here.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+CS2 = 1.0 / 3.0
+
+
+def moment_matrix(e, w):
+    """Rows: w-orthogonal polynomials of e, Gram-Schmidt in degree order;
+    returns (M, degree of each row)."""
+    q = len(w)
+    exps = sorted(itertools.product(range(3), repeat=3), key=lambda t: (sum(t), [-v for v in t]))
+    rows, degs = [], []
+    for a, b, c in exps:
+        v = (e[:, 0] ** a * e[:, 1] ** b * e[:, 2] ** c).astype(float)
+        for r in rows:
+            v = v - (w @ (v * r)) / (w @ (r * r)) * r
+        if w @ (v * v) > 1e-10:
+            rows.append(v)
+            degs.append(a + b + c)
+        if len(rows) == q:
+            break
+    M = np.array(rows)
+    assert M.shape == (q, q)
+    return M, np.array(degs)
+
+
+def shifted(f, d):
+    """f(x + d) on a periodic box, f of shape (nz, ny, nx), d = (dx, dy, dz)."""
+    return np.roll(f, shift=(-d[2], -d[1], -d[0]), axis=(0, 1, 2))
+
+
+def literal_step(prob, orc, h, g, phi_prev, u_prev):
+    e15, w15, _ = orc.lattice(15)
+    e, w, _ = orc.lattice(prob.q_hydro)
+    q = len(w)
+    tau_H, tau_L = prob.nu_H / CS2, prob.nu_L / CS2
+    omega = 1.0 / (prob.mobility / CS2 + 0.5)
+    beta, kappa = 12 * prob.sigma / prob.xi, 1.5 * prob.sigma * prob.xi
+
+    # ---- phase step
+    phi = h.sum(0)
+    G = sum(e15[i][:, None, None, None] * w15[i] * shifted(phi_prev, e15[i]) for i in range(15)) / CS2
+    Gn = np.sqrt((G ** 2).sum(0))
+    n = np.where(Gn ** 2 > 1e-24, G / np.where(Gn > 0, Gn, 1), 0.0)
+    theta = (1 - 4 * (phi_prev - 0.5) ** 2) / prob.xi
+    uu = (u_prev ** 2).sum(0)
+    h_next = np.zeros_like(h)
+    for i in range(15):
+        eu = np.einsum("a,a...->...", e15[i].astype(float), u_prev)
+        Gam = w15[i] * (1 + eu / CS2 + eu ** 2 / (2 * CS2 ** 2) - uu / (2 * CS2))
+        F = theta * w15[i] * np.einsum("a,a...->...", e15[i].astype(float), n)
+        hs = omega * (phi * Gam - h[i] - 0.5 * F) + h[i] + F
+        h_next[i] = shifted(hs, -e15[i])
+
+    # ---- hydro step on Phi^k = phi
+    M, deg = moment_matrix(e, w)
+    Minv = np.linalg.inv(M)
+    grad = sum(e[i][:, None, None, None] * w[i] * shifted(phi, e[i]) for i in range(q)) / CS2
+    lap = 2 * sum(w[i] * (shifted(phi, e[i]) - phi) for i in range(q)) / CS2
+    rho = prob.rho_L + phi * (prob.rho_H - prob.rho_L)
+    grad_rho = (prob.rho_H - prob.rho_L) * grad
+    tau = tau_L + phi * (tau_H - tau_L)
+    s_nu = 1 / (tau + 0.5)
+    mu = 4 * beta * phi * (phi - 1) * (phi - 0.5) - kappa * lap
+    pstar = g.sum(0)
+    F_p = -pstar * CS2 * grad_rho
+    F_s = mu * grad
+    F_b = (rho - prob.rho_ref)[None] * np.array(prob.gravity, dtype=float)[:, None, None, None]
+    j = np.einsum("ia,i...->a...", e.astype(float), g)
+
+    def geq(u):
+        uu = (u ** 2).sum(0)
+        out = []
+        for i in range(q):
+            eu = np.einsum("a,a...->...", e[i].astype(float), u)
+            Gam = w[i] * (1 + eu / CS2 + eu ** 2 / (2 * CS2 ** 2) - uu / (2 * CS2))
+            out.append(pstar * w[i] + (Gam - w[i]))
+        return np.array(out)
+
+    rates = lambda s: np.where(deg[:, None, None, None] == 2, s[None], 1.0)  # noqa: E731
+    S = rates(s_nu)
+    up = j + (F_p + F_s + F_b) / (2 * rho)
+    m = np.einsum("ki,i...->k...", M, g)
+    neq = np.einsum("ik,k...->i...", Minv, S * (m - np.einsum("ki,i...->k...", M, geq(up))))
+    Pi = np.einsum("ia,ib,i...->ab...", e.astype(float), e.astype(float), neq)
+    nu = tau * CS2
+    F_mu = -(nu / CS2) * np.einsum("ab...,b...->a...", Pi, grad_rho)
+    F = F_p + F_s + F_mu + F_b
+    u = j + F / (2 * rho)
+    m_eq = np.einsum("ki,i...->k...", M, geq(u))
+    F_m = np.zeros_like(m)
+    F_m[1:4] = F / rho
+    assert (deg[1:4] == 1).all()
+    m_star = m - S * (m - m_eq + 0.5 * F_m) + F_m
+    gs = np.einsum("ik,k...->i...", Minv, m_star)
+    g_next = np.array([shifted(gs[i], -e[i]) for i in range(q)])
+    return h_next, phi, g_next, u
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_literal_moment_space_step(orc, q):
+    prob = W.Problem(7, 6, 5, wall=(0, 0, 0), q_hydro=q, rho_ratio=100.0, mu_ratio=30.0, sigma=2e-3,
+                     xi=3.0, mobility=0.03, gravity=(2e-5, -3e-5, 1e-5), rho_ref=0.4)
+    p = orc.make_problem(prob)
+    rng = np.random.default_rng(11)
+    phi_prev = W.random_smooth_field(prob.shape, rng)
+    h = rng.uniform(0, 0.1, (15,) + prob.shape)
+    g = rng.normal(0, 1e-3, (q,) + prob.shape)
+    u_prev = rng.normal(0, 1e-2, (3,) + prob.shape)
+
+    h_lit, phi_lit, g_lit, u_lit = literal_step(prob, orc, h, g, phi_prev, u_prev)
+    h_next, phi_now = orc.phase_step(p, h, phi_prev, u_prev)
+    g_next, u_now = orc.hydro_step(p, g, phi_now)
+
+    assert np.abs(phi_now - phi_lit).max() < 1e-14
+    assert np.abs(h_next - h_lit).max() < 1e-14
+    assert np.abs(u_now - u_lit).max() < 1e-13 * max(1.0, np.abs(u_lit).max())
+    assert np.abs(g_next - g_lit).max() < 1e-13 * np.abs(g_lit).max()
+
+
+def test_moment_matrix_is_weighted_orthogonal(orc):
+    for q in (15, 19, 27):
+        e, w, _ = orc.lattice(q)
+        M, deg = moment_matrix(e, w)
+        N = M @ np.diag(w) @ M.T
+        assert np.abs(N - np.diag(np.diag(N))).max() < 1e-12
+        assert list(deg[:10]) == [0, 1, 1, 1, 2, 2, 2, 2, 2, 2]
