@@ -1,0 +1,165 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) conservative Allen-Cahn multiphase
+ * lattice Boltzmann solver.
+ *
+ * Method: Holzer, Bauer, Koestler, Ruede, "Highly efficient lattice Boltzmann
+ * multiphase simulations of immiscible fluids at high-density ratios on CPUs and
+ * GPUs through code generation", arXiv 2012.06144.
+ *   - phase-field LB on D3Q15 (Section 3.1, eq:lb_interface, eq:interfaceTracking,
+ *     eq:updatePhaseField), single-relaxation-time collision with rate
+ *     omega_phi = 1/(3 M + 1/2);
+ *   - velocity-based hydrodynamic LB on D3Q19 or D3Q27 (Section 3.2, eq:lb_flow,
+ *     eq:forceHydro ... eq:updateVelocityField), weighted-orthogonal MRT with the
+ *     force applied in moment space (eq:improved_collision);
+ *   - isotropic stencils eq:grad and eq:lap;
+ *   - one coupled time step = phase step then hydro step (Algorithm 2).
+ *
+ * Conventions shared by every entry point
+ *   - Cells: index c = x + nx*(y + ny*z), x fastest.  Scalar fields are nx*ny*nz
+ *     floats; vector fields are three such planes (x, y, z components).
+ *   - Populations: structure of arrays, plane i holds direction i for all cells.
+ *     Direction numbering (both lattices): 0 = rest; 1..6 = +x,-x,+y,-y,+z,-z;
+ *     D3Q19/D3Q27 then 7..18 = edges (+x+y,-x-y,+x-y,-x+y, +x+z,-x-z,+x-z,-x+z,
+ *     +y+z,-y-z,+y-z,-y+z); D3Q27 then 19..26 = corners (+++,---,++-,--+,+-+,-+-,
+ *     -++,+--).  D3Q15 = rest, the six faces, then the eight corners as 7..14 in
+ *     the same corner order.  Each moving direction is followed by its opposite.
+ *   - Walls: wall[a] = 1 puts no-slip walls (half-way bounce-back for h and g,
+ *     mirrored ghost values of phi in the stencils) on both faces of axis a;
+ *     wall[a] = 0 makes axis a periodic.
+ *   - Pointers flagged "on_device" are device pointers (any CUDA allocation
+ *     visible to the library's device); otherwise they are host pointers.  The
+ *     caller owns every buffer it passes; the library never frees or retains
+ *     them beyond the call.
+ *   - Every call is enqueued on the stream given to lbm_create.  Calls that
+ *     return data to host memory synchronise that stream before returning.
+ *   - No call aborts, exits or traps.  Invalid arguments return LBM_ERR_ARG
+ *     before anything is launched; CUDA failures return LBM_ERR_CUDA; the text
+ *     of the last failure is available from lbm_last_error.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_t lbm_t; /* opaque simulation handle */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,      /* invalid argument or parameter                       */
+    LBM_ERR_CUDA = -2,     /* a CUDA runtime call or kernel launch failed          */
+    LBM_ERR_OOM = -3,      /* workspace too small or allocation failed             */
+    LBM_ERR_DIVERGED = -4, /* a non-finite phi or p* was produced on the device    */
+    LBM_ERR_STATE = -5     /* call out of order (e.g. lbm_step before initialising) */
+} lbm_status;
+
+enum { LBM_PRECISION_FP32 = 0 };
+
+/* Box and lattices (Section 3; Section 5 uses D3Q15 for h and D3Q27 for g). */
+typedef struct {
+    int nx, ny, nz; /* cells per axis, each >= 1, nx*ny*nz < 2^31,
+                       ny <= 524280, nz <= 65535 (launch-grid limits)       */
+    int wall[3];    /* 0 = periodic axis, 1 = no-slip walls on both faces       */
+    int q_phase;    /* must be 15                                               */
+    int q_hydro;    /* 19 or 27                                                 */
+} lbm_domain;
+
+/* Physical parameters in lattice units (Delta x = Delta t = 1, c_s^2 = 1/3). */
+typedef struct {
+    double rho_H;      /* heavy-fluid density (phi = 1), > 0                    */
+    double rho_ratio;  /* rho_H / rho_L, > 0                 (eq:density)       */
+    double nu_H;       /* heavy-fluid kinematic viscosity, > 0                  */
+    double mu_ratio;   /* mu_H / mu_L with mu = rho nu, > 0                      */
+    double sigma;      /* surface tension, >= 0: beta = 12 sigma/xi, kappa = 3 sigma xi/2 (eq:chemPot) */
+    double xi;         /* interface width, > 0                                   */
+    double mobility;   /* M = tau_phi c_s^2, > 0              (eq:mobility)      */
+    double gravity[3]; /* body-force acceleration g                              */
+    double rho_ref;    /* buoyancy F_b = (rho - rho_ref) g; rho_ref = 0 gives F_b = rho g */
+    int precision;     /* LBM_PRECISION_FP32                                     */
+} lbm_params;
+
+/* Diagnostics returned by lbm_reduce (FP64 accumulation).  "Light" weights a
+ * cell by (1 - phi), the light-phase fraction. */
+enum {
+    LBM_DIAG_MASS = 0,    /* sum phi                                               */
+    LBM_DIAG_MOM_X = 1,   /* sum rho u_x   (rho from eq:density)                   */
+    LBM_DIAG_MOM_Y = 2,
+    LBM_DIAG_MOM_Z = 3,
+    LBM_DIAG_LIGHT_VOL = 4,  /* sum (1 - phi)                                      */
+    LBM_DIAG_LIGHT_X = 5,    /* sum (x + 1/2)(1 - phi) / sum (1 - phi): centroid   */
+    LBM_DIAG_LIGHT_Y = 6,
+    LBM_DIAG_LIGHT_Z = 7,
+    LBM_DIAG_LIGHT_UX = 8,   /* sum u_x (1 - phi) / sum (1 - phi): rise velocity   */
+    LBM_DIAG_LIGHT_UY = 9,
+    LBM_DIAG_LIGHT_UZ = 10,
+    LBM_DIAG_MAX_U = 11,     /* max |u|                                            */
+    LBM_DIAG_COUNT = 12
+};
+
+/* Bytes of device workspace lbm_create needs for this problem (populations h
+ * and g, two phi buffers, flags and reduction scratch).  Host-only; never
+ * touches the GPU. */
+lbm_status lbm_workspace_size(const lbm_domain *dom, const lbm_params *prm, size_t *bytes);
+
+/* Validates the problem (Section 3 parameters; LBM_ERR_ARG on a non-positive
+ * size, q_phase != 15, q_hydro not 19/27, non-positive densities, viscosities,
+ * xi or mobility, negative sigma, non-finite values), derives tau_H, tau_L,
+ * omega_phi, beta, kappa and creates a handle on the current CUDA device.
+ * cuda_stream: a cudaStream_t to enqueue all work on, or NULL for the legacy
+ * default stream.  workspace: a device buffer of at least lbm_workspace_size()
+ * bytes, 256-byte aligned, owned by the caller and kept alive until
+ * lbm_destroy; or NULL to let the library allocate (and later free) it. */
+lbm_status lbm_create(lbm_t **out, const lbm_domain *dom, const lbm_params *prm, void *cuda_stream,
+                      void *workspace, size_t workspace_bytes);
+
+/* Initial state from a phase field phi0 (nx*ny*nz floats): h_i = w_i phi0
+ * (= phi0 Gamma_i at rest), g_i = 0 (p* = 0, u = 0).  Runs the first phase-field
+ * step so that the handle holds time level 0.  Resets the step counter. */
+lbm_status lbm_init_phase(lbm_t *s, const float *phi0, int phi0_on_device);
+
+/* Advances n >= 0 coupled time steps (Algorithm 2: phase step, hydro step).
+ * Asynchronous: returns after enqueueing. */
+lbm_status lbm_step(lbm_t *s, int64_t n);
+
+/* Macroscopic fields at the current time level t: phi = sum_i h_i
+ * (eq:updatePhaseField), u = sum_i g_i e_i + F/(2 rho) (eq:updateVelocityField),
+ * p = p* rho c_s^2 (p* = sum_i g_i).  Any output may be NULL.  u is three
+ * planes.  Host outputs synchronise the stream. */
+lbm_status lbm_get_fields(lbm_t *s, float *phi, float *u, float *p, int on_device);
+
+/* LBM_DIAG_COUNT doubles into host memory (see the LBM_DIAG_* indices);
+ * synchronises the stream. */
+lbm_status lbm_reduce(lbm_t *s, double *out);
+
+/* Full state at time level t, pre-collision, in the natural population layout
+ * above: h = h^{t+1} (15 planes; the phase field runs one step ahead, see
+ * Algorithm 2), g = g^t (q_hydro planes), phi = phi^t.  Any output may be NULL.
+ * lbm_set_state takes the same three arrays (none may be NULL) and makes them
+ * the current state; it also marks the handle initialised.  Checkpoint and
+ * restart use the pair. */
+lbm_status lbm_get_state(lbm_t *s, float *h, float *g, float *phi, int on_device);
+lbm_status lbm_set_state(lbm_t *s, const float *h, const float *g, const float *phi, int on_device);
+
+/* Waits for the stream; returns LBM_ERR_DIVERGED once any step has produced a
+ * non-finite phi or p*. */
+lbm_status lbm_synchronize(lbm_t *s);
+
+/* Number of time steps advanced since lbm_init_phase (or lbm_set_state). */
+int64_t lbm_steps_done(const lbm_t *s);
+
+/* Text of the last failure on this handle; with s == NULL, of the last failed
+ * lbm_create on the calling thread. */
+const char *lbm_last_error(const lbm_t *s);
+
+/* Releases the handle and, if the library allocated it, the workspace. */
+void lbm_destroy(lbm_t *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

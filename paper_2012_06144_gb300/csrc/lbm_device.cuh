@@ -1,0 +1,318 @@
+// lbm_device.cuh -- device building blocks of the coupled conservative
+// Allen-Cahn LBM step (arXiv 2012.06144, Section 3) for sm_103a.
+//
+// Storage: one in-place copy per lattice, structure of arrays (plane i =
+// direction i), streamed with the AA access pattern.  A lattice is either in
+// natural layout (plane i at cell x holds f_i(x), pre-collision) or in swapped
+// layout (plane opp(i) at x holds the post-collision f*_i(x) that still has to
+// move to x + e_i).  A step on a natural lattice reads f_i(x) from (i, x) and
+// writes f*_i(x) to (opp(i), x); a step on a swapped lattice reads f_i(x) from
+// (opp(i), x - e_i) and writes f*_i(x) to (i, x + e_i).  Every thread reads and
+// writes exactly the same locations, so the update is race-free in place.
+// Walls use half-way bounce-back: a population whose source x - e_i (or
+// destination x + e_i) lies beyond a walled face is read from (i, x) (written
+// to (opp(i), x)) instead.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace lbm {
+
+struct V3 {
+    int x, y, z;
+};
+
+// D3Q27 velocities in the documented numbering: rest, faces, edges, corners,
+// each moving direction followed by its opposite.
+__host__ __device__ constexpr V3 vel27(int i) {
+    switch (i) {
+        case 0: return {0, 0, 0};
+        case 1: return {1, 0, 0};
+        case 2: return {-1, 0, 0};
+        case 3: return {0, 1, 0};
+        case 4: return {0, -1, 0};
+        case 5: return {0, 0, 1};
+        case 6: return {0, 0, -1};
+        case 7: return {1, 1, 0};
+        case 8: return {-1, -1, 0};
+        case 9: return {1, -1, 0};
+        case 10: return {-1, 1, 0};
+        case 11: return {1, 0, 1};
+        case 12: return {-1, 0, -1};
+        case 13: return {1, 0, -1};
+        case 14: return {-1, 0, 1};
+        case 15: return {0, 1, 1};
+        case 16: return {0, -1, -1};
+        case 17: return {0, 1, -1};
+        case 18: return {0, -1, 1};
+        case 19: return {1, 1, 1};
+        case 20: return {-1, -1, -1};
+        case 21: return {1, 1, -1};
+        case 22: return {-1, -1, 1};
+        case 23: return {1, -1, 1};
+        case 24: return {-1, 1, -1};
+        case 25: return {-1, 1, 1};
+        default: return {1, -1, -1};
+    }
+}
+
+// D3Q15 = rest, six faces, eight corners; D3Q19 = first 19 of D3Q27.
+template <int Q>
+__host__ __device__ constexpr V3 vel(int i) {
+    return (Q == 15 && i >= 7) ? vel27(i + 12) : vel27(i);
+}
+
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// Lattice weights selected by |e|^2.
+template <int Q>
+__host__ __device__ constexpr float wgt(int i) {
+    const V3 e = vel<Q>(i);
+    const int e2 = e.x * e.x + e.y * e.y + e.z * e.z;
+    if (Q == 15) return e2 == 0 ? 2.0f / 9.0f : (e2 == 1 ? 1.0f / 9.0f : 1.0f / 72.0f);
+    if (Q == 19) return e2 == 0 ? 1.0f / 3.0f : (e2 == 1 ? 1.0f / 18.0f : 1.0f / 36.0f);
+    return e2 == 0 ? 8.0f / 27.0f : (e2 == 1 ? 2.0f / 27.0f : (e2 == 2 ? 1.0f / 54.0f : 1.0f / 216.0f));
+}
+
+// Kernel-side copy of the problem (derived in lbm_create).
+struct Params {
+    int nx, ny, nz;
+    int wall;  // bit a set: axis a has walls on both faces
+    long long N;
+    float rho_L, drho;  // rho = rho_L + phi * (rho_H - rho_L)        (eq:density)
+    float tau_L, dtau;  // tau = tau_L + phi * (tau_H - tau_L)
+    float omega_phi;    // 1 / (tau_phi + 1/2), tau_phi = M / c_s^2
+    float beta4;        // 4 beta, beta = 12 sigma / xi
+    float kappa;        // 3 sigma xi / 2
+    float inv_xi;
+    float gx, gy, gz, rho_ref;
+};
+
+// Per-thread geometry: neighbour offsets along each axis (periodic wrap, or
+// clamp at a walled face, which is the mirrored ghost value for phi) and the
+// walled faces the cell touches.
+struct Cell {
+    int c;
+    int xo[3], yo[3], zo[3];
+    int lo, hi;  // bit a: cell on the low / high walled face of axis a
+};
+
+__device__ __forceinline__ int wrap_or_clamp(int v, int n, bool walled) {
+    if (v < 0) return walled ? 0 : n - 1;
+    if (v >= n) return walled ? n - 1 : 0;
+    return v;
+}
+
+__device__ __forceinline__ Cell make_cell(const Params &p, int x, int y, int z) {
+    Cell C;
+    const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
+    const int nxy = p.nx * p.ny;
+    C.c = x + p.nx * (y + p.ny * z);
+    C.xo[0] = wrap_or_clamp(x - 1, p.nx, wx);
+    C.xo[1] = x;
+    C.xo[2] = wrap_or_clamp(x + 1, p.nx, wx);
+    C.yo[0] = wrap_or_clamp(y - 1, p.ny, wy) * p.nx;
+    C.yo[1] = y * p.nx;
+    C.yo[2] = wrap_or_clamp(y + 1, p.ny, wy) * p.nx;
+    C.zo[0] = wrap_or_clamp(z - 1, p.nz, wz) * nxy;
+    C.zo[1] = z * nxy;
+    C.zo[2] = wrap_or_clamp(z + 1, p.nz, wz) * nxy;
+    C.lo = (wx && x == 0 ? 1 : 0) | (wy && y == 0 ? 2 : 0) | (wz && z == 0 ? 4 : 0);
+    C.hi = (wx && x == p.nx - 1 ? 1 : 0) | (wy && y == p.ny - 1 ? 2 : 0) | (wz && z == p.nz - 1 ? 4 : 0);
+    return C;
+}
+
+__device__ __forceinline__ int nbr(const Cell &C, int dx, int dy, int dz) {
+    return C.xo[dx + 1] + C.yo[dy + 1] + C.zo[dz + 1];
+}
+
+// True if x - e (sign = -1) or x + e (sign = +1) leaves the box through a wall.
+__device__ __forceinline__ bool leaves(const Cell &C, V3 e, int sign) {
+    const int ex = e.x * sign, ey = e.y * sign, ez = e.z * sign;
+    return (ex > 0 && (C.hi & 1)) || (ex < 0 && (C.lo & 1)) || (ey > 0 && (C.hi & 2)) || (ey < 0 && (C.lo & 2)) ||
+           (ez > 0 && (C.hi & 4)) || (ez < 0 && (C.lo & 4));
+}
+
+// Location (plane, cell) holding the pre-collision f_i(x) of a lattice.
+template <int Q, bool SWAPPED>
+__device__ __forceinline__ size_t pop_src(const Cell &C, long long N, int i) {
+    if (!SWAPPED) return (size_t)i * N + C.c;
+    const V3 e = vel<Q>(i);
+    if (leaves(C, e, -1)) return (size_t)i * N + C.c;
+    return (size_t)opp(i) * N + nbr(C, -e.x, -e.y, -e.z);
+}
+
+// Location that receives the post-collision f*_i(x).
+template <int Q, bool SWAPPED>
+__device__ __forceinline__ size_t pop_dst(const Cell &C, long long N, int i) {
+    if (!SWAPPED) return (size_t)opp(i) * N + C.c;
+    const V3 e = vel<Q>(i);
+    if (leaves(C, e, +1)) return (size_t)opp(i) * N + C.c;
+    return (size_t)i * N + nbr(C, e.x, e.y, e.z);
+}
+
+// The 3x3x3 neighbourhood of phi, nb[(dz+1)*9 + (dy+1)*3 + (dx+1)].
+__device__ __forceinline__ void gather_phi(const float *__restrict__ phi, const Cell &C, float nb[27]) {
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = __ldg(phi + nbr(C, dx, dy, dz));
+}
+
+template <int Q>
+__device__ __forceinline__ float nb_at(const float nb[27], int i) {
+    const V3 e = vel<Q>(i);
+    return nb[(e.z + 1) * 9 + (e.y + 1) * 3 + (e.x + 1)];
+}
+
+// eq:grad: grad phi = (1/c_s^2) sum_i w_i e_i phi(x + e_i).
+template <int Q>
+__device__ __forceinline__ void stencil_grad(const float nb[27], float &gx, float &gy, float &gz) {
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const V3 e = vel<Q>(i);
+        const float v = wgt<Q>(i) * nb_at<Q>(nb, i);
+        if (e.x) sx += e.x > 0 ? v : -v;
+        if (e.y) sy += e.y > 0 ? v : -v;
+        if (e.z) sz += e.z > 0 ? v : -v;
+    }
+    gx = 3.f * sx;
+    gy = 3.f * sy;
+    gz = 3.f * sz;
+}
+
+// eq:lap: lap phi = (2/c_s^2) sum_i w_i (phi(x + e_i) - phi(x)).
+template <int Q>
+__device__ __forceinline__ float stencil_lap(const float nb[27]) {
+    const float c = nb[13];
+    float s = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) s += wgt<Q>(i) * (nb_at<Q>(nb, i) - c);
+    return 6.f * s;
+}
+
+// Macroscopic quantities and forces of the hydrodynamic step at one cell
+// (Section 3.2).  Input: the pre-collision g_i(x) and the phi neighbourhood.
+template <int QG>
+struct Hydro {
+    float pstar, ux, uy, uz;   // p* and u (eq:updateVelocityField)
+    float Fx, Fy, Fz;          // total force (eq:forceHydro)
+    float half_inv_rho;        // 1 / (2 rho)
+    float s_nu;
+    float a2xx, a2yy, a2zz, a2xy, a2xz, a2yz;  // Hermite second moments sum g (e e - c_s^2 I)
+    float rho;
+};
+
+template <int QG>
+__device__ __forceinline__ void hydro_macro(const Params &p, const float gv[QG], const float nb[27], Hydro<QG> &H) {
+    // moments of g
+    float ps = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;
+#pragma unroll
+    for (int i = 0; i < QG; ++i) {
+        const V3 e = vel<QG>(i);
+        const float v = gv[i];
+        ps += v;
+        if (e.x) { jx += e.x > 0 ? v : -v; mxx += v; }
+        if (e.y) { jy += e.y > 0 ? v : -v; myy += v; }
+        if (e.z) { jz += e.z > 0 ? v : -v; mzz += v; }
+        if (e.x && e.y) mxy += (e.x * e.y > 0) ? v : -v;
+        if (e.x && e.z) mxz += (e.x * e.z > 0) ? v : -v;
+        if (e.y && e.z) myz += (e.y * e.z > 0) ? v : -v;
+    }
+    const float phi = nb[13];
+    float gpx, gpy, gpz;
+    stencil_grad<QG>(nb, gpx, gpy, gpz);
+    const float lap = stencil_lap<QG>(nb);
+
+    const float rho = p.rho_L + phi * p.drho;  // eq:density
+    const float hir = 0.5f / rho;
+    const float tau = p.tau_L + phi * p.dtau;
+    const float s_nu = 1.0f / (tau + 0.5f);
+    const float grx = p.drho * gpx, gry = p.drho * gpy, grz = p.drho * gpz;
+
+    // eq:chemPot, eq:surfaceTension
+    const float mu = p.beta4 * phi * (phi - 1.0f) * (phi - 0.5f) - p.kappa * lap;
+    // eq:pressure_force, buoyancy
+    const float cp = -ps * (1.0f / 3.0f);
+    const float db = rho - p.rho_ref;
+    const float f0x = mu * gpx + cp * grx + db * p.gx;
+    const float f0y = mu * gpy + cp * gry + db * p.gy;
+    const float f0z = mu * gpz + cp * grz + db * p.gz;
+
+    // non-equilibrium second moments with u' (all forces but F_mu)
+    const float upx = jx + f0x * hir, upy = jy + f0y * hir, upz = jz + f0z * hir;
+    const float c3 = ps * (1.0f / 3.0f);
+    const float a2xx = mxx - c3, a2yy = myy - c3, a2zz = mzz - c3;
+    const float pxx = a2xx - upx * upx, pyy = a2yy - upy * upy, pzz = a2zz - upz * upz;
+    const float pxy = mxy - upx * upy, pxz = mxz - upx * upz, pyz = myz - upy * upz;
+    // eq:viscousForce: F_mu = -(nu / c_s^2) s_nu Pi_neq . grad rho = -tau s_nu Pi_neq . grad rho
+    const float cm = -tau * s_nu;
+    const float Fx = f0x + cm * (pxx * grx + pxy * gry + pxz * grz);
+    const float Fy = f0y + cm * (pxy * grx + pyy * gry + pyz * grz);
+    const float Fz = f0z + cm * (pxz * grx + pyz * gry + pzz * grz);
+
+    H.pstar = ps;
+    H.ux = jx + Fx * hir;
+    H.uy = jy + Fy * hir;
+    H.uz = jz + Fz * hir;
+    H.Fx = Fx;
+    H.Fy = Fy;
+    H.Fz = Fz;
+    H.half_inv_rho = hir;
+    H.s_nu = s_nu;
+    H.a2xx = a2xx;
+    H.a2yy = a2yy;
+    H.a2zz = a2zz;
+    H.a2xy = mxy;
+    H.a2xz = mxz;
+    H.a2yz = myz;
+    H.rho = rho;
+}
+
+// Post-collision population i of eq:improved_collision in Hermite form:
+// zeroth moment p*, first moments u + F/(2 rho), second (Hermite) moments
+// (1 - s_nu) a2 + s_nu u u, every higher moment 0.
+template <int QG>
+struct HydroPost {
+    float m0, m1x, m1y, m1z, bxx, byy, bzz, bxy, bxz, byz, tr3;
+};
+
+template <int QG>
+__device__ __forceinline__ HydroPost<QG> hydro_post(const Hydro<QG> &H) {
+    HydroPost<QG> P;
+    const float s = H.s_nu, r = 1.0f - s;
+    P.m0 = H.pstar;
+    P.m1x = 3.0f * (H.ux + H.Fx * H.half_inv_rho);
+    P.m1y = 3.0f * (H.uy + H.Fy * H.half_inv_rho);
+    P.m1z = 3.0f * (H.uz + H.Fz * H.half_inv_rho);
+    const float bxx = r * H.a2xx + s * H.ux * H.ux;
+    const float byy = r * H.a2yy + s * H.uy * H.uy;
+    const float bzz = r * H.a2zz + s * H.uz * H.uz;
+    P.bxx = 4.5f * bxx;
+    P.byy = 4.5f * byy;
+    P.bzz = 4.5f * bzz;
+    P.bxy = 9.0f * (r * H.a2xy + s * H.ux * H.uy);
+    P.bxz = 9.0f * (r * H.a2xz + s * H.ux * H.uz);
+    P.byz = 9.0f * (r * H.a2yz + s * H.uy * H.uz);
+    P.tr3 = 1.5f * (bxx + byy + bzz);  // 4.5 * trace / 3
+    return P;
+}
+
+template <int QG>
+__device__ __forceinline__ float hydro_gstar(const HydroPost<QG> &P, int i) {
+    const V3 e = vel<QG>(i);
+    float s = P.m0 - P.tr3;
+    if (e.x) s += (e.x > 0 ? P.m1x : -P.m1x) + P.bxx;
+    if (e.y) s += (e.y > 0 ? P.m1y : -P.m1y) + P.byy;
+    if (e.z) s += (e.z > 0 ? P.m1z : -P.m1z) + P.bzz;
+    if (e.x && e.y) s += (e.x * e.y > 0) ? P.bxy : -P.bxy;
+    if (e.x && e.z) s += (e.x * e.z > 0) ? P.bxz : -P.bxz;
+    if (e.y && e.z) s += (e.y * e.z > 0) ? P.byz : -P.byz;
+    return wgt<QG>(i) * s;
+}
+
+}  // namespace lbm

@@ -1,0 +1,115 @@
+// lbm_step.cu -- the fused coupled step of the conservative Allen-Cahn LBM.
+//
+// One launch K_k advances every cell by the hydrodynamic step k-1 and the
+// phase-field step k of Algorithm 2 (arXiv 2012.06144, Section 4.2):
+//   hydro(k-1): from g^{k-1}(x) and the stored field phi^{k-1} (27-point
+//               neighbourhood): p*, rho, tau, s_nu, F_s, F_p, F_b, F_mu, u_{k-1}
+//               (Section 3.2), weighted-orthogonal MRT collision with moment-space
+//               forcing (eq:improved_collision), AA streaming of g;
+//   phase(k):   phi_k = sum_i h_i^k (eq:updatePhaseField), written to the other
+//               phi buffer; normal and theta from phi^{k-1} (eq:interfaceTracking),
+//               h^eq = phi_k Gamma_i(u_{k-1}) with u_{k-1} straight from the
+//               hydro part in registers, SRT collision (eq:lb_interface), AA
+//               streaming of h.
+// The same stencil field phi^{k-1} serves both halves, so one pass reads
+// 15 h + q g + phi and writes 15 h + q g + phi per cell, and no velocity field is
+// stored.  The h lattice runs one time level ahead of g.
+#include "lbm_internal.h"
+
+namespace lbm {
+
+template <int QG, bool G_SW, bool H_SW, bool HYDRO>
+__global__ void __launch_bounds__(256) fused_step_kernel(Params p, float *__restrict__ h, float *__restrict__ g,
+                                                         const float *__restrict__ phi_in,
+                                                         float *__restrict__ phi_out, int *__restrict__ flag) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const Cell C = make_cell(p, x, y, z);
+    const long long N = p.N;
+
+    float nb[27];
+    gather_phi(phi_in, C, nb);
+    float gv[QG];
+    if (HYDRO) {
+#pragma unroll
+        for (int i = 0; i < QG; ++i) gv[i] = g[pop_src<QG, G_SW>(C, N, i)];
+    }
+    float hv[15];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) hv[i] = h[pop_src<15, H_SW>(C, N, i)];
+
+    // ---- hydrodynamic step k-1
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    if (HYDRO) {
+        Hydro<QG> Hd;
+        hydro_macro<QG>(p, gv, nb, Hd);
+        const HydroPost<QG> P = hydro_post<QG>(Hd);
+#pragma unroll
+        for (int i = 0; i < QG; ++i) g[pop_dst<QG, G_SW>(C, N, i)] = hydro_gstar<QG>(P, i);
+        ux = Hd.ux;
+        uy = Hd.uy;
+        uz = Hd.uz;
+        if (!(fabsf(Hd.pstar) < 1e30f)) *flag = 1;
+    }
+
+    // ---- phase-field step k
+    float phik = 0.f;
+#pragma unroll
+    for (int i = 0; i < 15; ++i) phik += hv[i];
+    phi_out[C.c] = phik;
+    if (!(fabsf(phik) < 1e30f)) *flag = 1;
+
+    float Gx, Gy, Gz;
+    stencil_grad<15>(nb, Gx, Gy, Gz);
+    const float G2 = Gx * Gx + Gy * Gy + Gz * Gz;
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    if (G2 > 1e-24f) {
+        const float inv = rsqrtf(G2);
+        nx = Gx * inv;
+        ny = Gy * inv;
+        nz = Gz * inv;
+    }
+    const float pc = nb[13] - 0.5f;
+    const float theta = (1.0f - 4.0f * pc * pc) * p.inv_xi;
+    const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float om = p.omega_phi, fc = 1.0f - 0.5f * om;
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+        const V3 e = vel<15>(i);
+        const float w = wgt<15>(i);
+        const float eu = e.x * ux + e.y * uy + e.z * uz;
+        const float en = e.x * nx + e.y * ny + e.z * nz;
+        const float heq = phik * w * (1.0f + 3.0f * eu + 4.5f * eu * eu - uu);
+        const float F = theta * w * en;
+        h[pop_dst<15, H_SW>(C, N, i)] = hv[i] + om * (heq - hv[i]) + fc * F;
+    }
+}
+
+template <int QG, bool G_SW, bool H_SW, bool HYDRO>
+static cudaError_t launch(const Params &p, float *h, float *g, const float *pi, float *po, int *flag,
+                          cudaStream_t st) {
+    const dim3 block(32, 8, 1);
+    const dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, p.nz);
+    fused_step_kernel<QG, G_SW, H_SW, HYDRO><<<grid, block, 0, st>>>(p, h, g, pi, po, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const Params &p, int q_hydro, bool g_sw, bool h_sw, bool hydro, float *h, float *g,
+                        const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
+    if (!hydro) {
+        if (h_sw) return cudaErrorInvalidValue;  // the first phase step starts from natural h
+        return launch<19, false, false, false>(p, h, g, phi_in, phi_out, flag, st);
+    }
+    if (g_sw == h_sw) return cudaErrorInvalidValue;  // h runs one AA step ahead of g
+    if (q_hydro == 19)
+        return g_sw ? launch<19, true, false, true>(p, h, g, phi_in, phi_out, flag, st)
+                    : launch<19, false, true, true>(p, h, g, phi_in, phi_out, flag, st);
+    if (q_hydro == 27)
+        return g_sw ? launch<27, true, false, true>(p, h, g, phi_in, phi_out, flag, st)
+                    : launch<27, false, true, true>(p, h, g, phi_in, phi_out, flag, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

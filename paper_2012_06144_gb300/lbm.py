@@ -1,0 +1,291 @@
+"""ctypes binding of the C ABI in include/lbm.h (argument marshalling only).
+
+The functions below carry the C names and forward plain pointers and sizes;
+every computation runs in the CUDA library.  ``Simulation`` is a small
+convenience wrapper that takes its device workspace and its stream from
+PyTorch.  There is no CPU fallback: if the library is not built, loading
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import _build
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_STATE = 0, -1, -2, -3, -4, -5
+STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM", -4: "LBM_ERR_DIVERGED",
+                -5: "LBM_ERR_STATE"}
+LBM_PRECISION_FP32 = 0
+DIAG_NAMES = ["mass", "mom_x", "mom_y", "mom_z", "light_vol", "light_x", "light_y", "light_z", "light_ux",
+              "light_uy", "light_uz", "max_u"]
+LBM_DIAG_COUNT = len(DIAG_NAMES)
+
+
+class lbm_domain(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("wall", ctypes.c_int * 3),
+                ("q_phase", ctypes.c_int), ("q_hydro", ctypes.c_int)]
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("rho_H", ctypes.c_double), ("rho_ratio", ctypes.c_double), ("nu_H", ctypes.c_double),
+                ("mu_ratio", ctypes.c_double), ("sigma", ctypes.c_double), ("xi", ctypes.c_double),
+                ("mobility", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("rho_ref", ctypes.c_double),
+                ("precision", ctypes.c_int)]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+_VP, _FP, _DP = ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+_SIGNATURES = {
+    "lbm_workspace_size": ([ctypes.POINTER(lbm_domain), ctypes.POINTER(lbm_params), ctypes.POINTER(ctypes.c_size_t)],
+                           ctypes.c_int),
+    "lbm_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(lbm_domain), ctypes.POINTER(lbm_params), _VP, _VP,
+                    ctypes.c_size_t], ctypes.c_int),
+    "lbm_init_phase": ([_VP, _FP, ctypes.c_int], ctypes.c_int),
+    "lbm_step": ([_VP, ctypes.c_int64], ctypes.c_int),
+    "lbm_get_fields": ([_VP, _FP, _FP, _FP, ctypes.c_int], ctypes.c_int),
+    "lbm_reduce": ([_VP, _DP], ctypes.c_int),
+    "lbm_get_state": ([_VP, _FP, _FP, _FP, ctypes.c_int], ctypes.c_int),
+    "lbm_set_state": ([_VP, _FP, _FP, _FP, ctypes.c_int], ctypes.c_int),
+    "lbm_synchronize": ([_VP], ctypes.c_int),
+    "lbm_steps_done": ([_VP], ctypes.c_int64),
+    "lbm_last_error": ([_VP], ctypes.c_char_p),
+    "lbm_destroy": ([_VP], None),
+}
+
+
+def header_functions() -> list:
+    """Names of the functions declared in include/lbm.h."""
+    text = open(os.path.join(_build.INCLUDE, "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+
+
+def library_path() -> str:
+    return _build.LIBRARY
+
+
+def load():
+    """Loads liblbm.so (built by ``__graft_entry__.build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIBRARY):
+                raise RuntimeError(f"CUDA library not built: {_build.LIBRARY} (run __graft_entry__.build())")
+            lib = ctypes.CDLL(_build.LIBRARY)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+        return _lib
+
+
+def _check(status: int, handle=None):
+    if status != LBM_OK:
+        msg = load().lbm_last_error(handle)
+        raise LBMError(status, msg.decode() if msg else "")
+
+
+def make_domain(nx, ny, nz, wall=(0, 0, 0), q_hydro=27, q_phase=15) -> lbm_domain:
+    d = lbm_domain()
+    d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
+    for a in range(3):
+        d.wall[a] = int(wall[a])
+    d.q_phase, d.q_hydro = int(q_phase), int(q_hydro)
+    return d
+
+
+def make_params(rho_H=1.0, rho_ratio=1000.0, nu_H=0.01, mu_ratio=100.0, sigma=1e-4, xi=5.0, mobility=0.02,
+                gravity=(0.0, 0.0, 0.0), rho_ref=0.0, precision=LBM_PRECISION_FP32) -> lbm_params:
+    p = lbm_params()
+    p.rho_H, p.rho_ratio, p.nu_H, p.mu_ratio = float(rho_H), float(rho_ratio), float(nu_H), float(mu_ratio)
+    p.sigma, p.xi, p.mobility = float(sigma), float(xi), float(mobility)
+    for a in range(3):
+        p.gravity[a] = float(gravity[a])
+    p.rho_ref, p.precision = float(rho_ref), int(precision)
+    return p
+
+
+def from_problem(prob):
+    """(lbm_domain, lbm_params) of a ``workloads.Problem``-like object."""
+    d = make_domain(prob.nx, prob.ny, prob.nz, prob.wall, prob.q_hydro)
+    p = make_params(prob.rho_H, prob.rho_ratio, prob.nu_H, prob.mu_ratio, prob.sigma, prob.xi, prob.mobility,
+                    prob.gravity, prob.rho_ref)
+    return d, p
+
+
+# ---- the C functions, same names, pointers as Python ints -------------------------------------------
+
+
+def lbm_workspace_size(dom: lbm_domain, prm: lbm_params) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().lbm_workspace_size(ctypes.byref(dom), ctypes.byref(prm), ctypes.byref(n)))
+    return n.value
+
+
+def lbm_create(dom: lbm_domain, prm: lbm_params, stream: int = 0, workspace: int = 0, workspace_bytes: int = 0):
+    h = ctypes.c_void_p()
+    _check(load().lbm_create(ctypes.byref(h), ctypes.byref(dom), ctypes.byref(prm), stream or None, workspace or None,
+                             workspace_bytes))
+    return h
+
+
+def lbm_init_phase(h, phi0: int, on_device: int):
+    _check(load().lbm_init_phase(h, phi0, on_device), h)
+
+
+def lbm_step(h, n: int):
+    _check(load().lbm_step(h, int(n)), h)
+
+
+def lbm_get_fields(h, phi: int, u: int, p: int, on_device: int):
+    _check(load().lbm_get_fields(h, phi or None, u or None, p or None, on_device), h)
+
+
+def lbm_reduce(h) -> np.ndarray:
+    out = np.zeros(LBM_DIAG_COUNT)
+    _check(load().lbm_reduce(h, out.ctypes.data_as(_DP)), h)
+    return out
+
+
+def lbm_get_state(h, hp: int, gp: int, phip: int, on_device: int):
+    _check(load().lbm_get_state(h, hp or None, gp or None, phip or None, on_device), h)
+
+
+def lbm_set_state(h, hp: int, gp: int, phip: int, on_device: int):
+    _check(load().lbm_set_state(h, hp, gp, phip, on_device), h)
+
+
+def lbm_synchronize(h):
+    _check(load().lbm_synchronize(h), h)
+
+
+def lbm_steps_done(h) -> int:
+    return int(load().lbm_steps_done(h))
+
+
+def lbm_last_error(h=None) -> str:
+    m = load().lbm_last_error(h)
+    return m.decode() if m else ""
+
+
+def lbm_destroy(h):
+    load().lbm_destroy(h)
+
+
+# ---- convenience wrapper: device memory and stream from PyTorch --------------------------------------
+
+
+class Simulation:
+    """One simulation on the current CUDA device.  Workspace = a torch uint8
+    tensor; all work goes to torch's current stream (or ``stream``)."""
+
+    def __init__(self, domain: lbm_domain, params: lbm_params, stream=None, device=None):
+        import torch
+
+        self.torch = torch
+        self.domain, self.params = domain, params
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.nbytes = lbm_workspace_size(domain, params)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            base = self.workspace.data_ptr()
+            aligned = (base + 255) & ~255
+            self.handle = lbm_create(domain, params, self.stream.cuda_stream, aligned, self.nbytes)
+        self.shape = (domain.nz, domain.ny, domain.nx)
+        self.N = domain.nx * domain.ny * domain.nz
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        d, p = from_problem(prob)
+        return cls(d, p, **kw)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, t):
+        assert t.is_cuda and t.is_contiguous() and t.dtype == self.torch.float32
+        return t.data_ptr()
+
+    def init_phase(self, phi0):
+        if isinstance(phi0, np.ndarray):
+            a = np.ascontiguousarray(phi0, dtype=np.float32)
+            assert a.size == self.N
+            lbm_init_phase(self.handle, a.ctypes.data, 0)
+        else:
+            assert phi0.numel() == self.N
+            lbm_init_phase(self.handle, self._dev(phi0), 1)
+
+    def step(self, n: int = 1):
+        lbm_step(self.handle, n)
+
+    def steps_done(self) -> int:
+        return lbm_steps_done(self.handle)
+
+    def synchronize(self):
+        lbm_synchronize(self.handle)
+
+    def fields(self, on_device: bool = True):
+        """(phi, u, p) as torch tensors (device) or numpy arrays (host)."""
+        if on_device:
+            t = self.torch
+            phi = t.empty(self.shape, device=self.device)
+            u = t.empty((3,) + self.shape, device=self.device)
+            p = t.empty(self.shape, device=self.device)
+            lbm_get_fields(self.handle, phi.data_ptr(), u.data_ptr(), p.data_ptr(), 1)
+            return phi, u, p
+        phi = np.empty(self.shape, np.float32)
+        u = np.empty((3,) + self.shape, np.float32)
+        p = np.empty(self.shape, np.float32)
+        lbm_get_fields(self.handle, phi.ctypes.data, u.ctypes.data, p.ctypes.data, 0)
+        return phi, u, p
+
+    def reduce(self) -> dict:
+        return dict(zip(DIAG_NAMES, lbm_reduce(self.handle)))
+
+    def get_state(self, on_device: bool = False):
+        q = self.domain.q_hydro
+        if on_device:
+            t = self.torch
+            h = t.empty((15,) + self.shape, device=self.device)
+            g = t.empty((q,) + self.shape, device=self.device)
+            phi = t.empty(self.shape, device=self.device)
+            lbm_get_state(self.handle, h.data_ptr(), g.data_ptr(), phi.data_ptr(), 1)
+            return h, g, phi
+        h = np.empty((15,) + self.shape, np.float32)
+        g = np.empty((q,) + self.shape, np.float32)
+        phi = np.empty(self.shape, np.float32)
+        lbm_get_state(self.handle, h.ctypes.data, g.ctypes.data, phi.ctypes.data, 0)
+        return h, g, phi
+
+    def set_state(self, h, g, phi):
+        if isinstance(h, np.ndarray):
+            h = np.ascontiguousarray(h, dtype=np.float32)
+            g = np.ascontiguousarray(g, dtype=np.float32)
+            phi = np.ascontiguousarray(phi, dtype=np.float32)
+            assert h.size == 15 * self.N and g.size == self.domain.q_hydro * self.N and phi.size == self.N
+            lbm_set_state(self.handle, h.ctypes.data, g.ctypes.data, phi.ctypes.data, 0)
+        else:
+            lbm_set_state(self.handle, self._dev(h), self._dev(g), self._dev(phi), 1)
