@@ -80,13 +80,16 @@ typedef struct {
     double gravity[3]; /* body-force acceleration g                              */
     double rho_ref;    /* buoyancy F_b = (rho - rho_ref) g; rho_ref = 0 gives F_b = rho g */
     int precision;     /* LBM_PRECISION_FP32                                     */
+    int clamp_phi;     /* 1: use phi clamped to [0, 1] inside rho and tau (keeps
+                          rho >= rho_L when phi undershoots at high density ratio);
+                          0: use phi as is                                       */
 } lbm_params;
 
 /* Diagnostics returned by lbm_reduce (FP64 accumulation).  "Light" weights a
  * cell by (1 - phi), the light-phase fraction. */
 enum {
     LBM_DIAG_MASS = 0,    /* sum phi                                               */
-    LBM_DIAG_MOM_X = 1,   /* sum rho u_x   (rho from eq:density)                   */
+    LBM_DIAG_MOM_X = 1,   /* sum rho u_x   (rho from eq:density, phi clamped if clamp_phi) */
     LBM_DIAG_MOM_Y = 2,
     LBM_DIAG_MOM_Z = 3,
     LBM_DIAG_LIGHT_VOL = 4,  /* sum (1 - phi)                                      */

@@ -116,7 +116,7 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def make_problem(prob, theta_from_local_phi: bool = False, clamp_phi: bool = False) -> orc_problem:
+def make_problem(prob, theta_from_local_phi: bool = False, clamp_phi=None) -> orc_problem:
     """Builds the C problem record from a ``workloads.Problem``-like object."""
     p = orc_problem()
     p.nx, p.ny, p.nz = int(prob.nx), int(prob.ny), int(prob.nz)
@@ -129,7 +129,7 @@ def make_problem(prob, theta_from_local_phi: bool = False, clamp_phi: bool = Fal
     p.sigma, p.xi, p.mobility = float(prob.sigma), float(prob.xi), float(prob.mobility)
     p.rho_ref = float(prob.rho_ref)
     p.theta_from_local_phi = int(theta_from_local_phi)
-    p.clamp_phi = int(clamp_phi)
+    p.clamp_phi = int(getattr(prob, "clamp_phi", 0) if clamp_phi is None else clamp_phi)
     return p
 
 

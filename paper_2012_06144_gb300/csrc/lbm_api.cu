@@ -85,6 +85,7 @@ lbm_status validate(const lbm_domain *d, const lbm_params *p, std::string &why) 
     if (p->xi <= 0) return why = "xi must be positive", LBM_ERR_ARG;
     if (p->mobility <= 0) return why = "mobility must be positive", LBM_ERR_ARG;
     if (p->precision != LBM_PRECISION_FP32) return why = "unsupported precision", LBM_ERR_ARG;
+    if (p->clamp_phi != 0 && p->clamp_phi != 1) return why = "clamp_phi must be 0 or 1", LBM_ERR_ARG;
     const double rho_L = p->rho_H / p->rho_ratio;
     const double nu_L = p->nu_H * p->rho_H / (p->mu_ratio * rho_L);
     if (!(rho_L > 0) || !finite(rho_L)) return why = "rho_L = rho_H / rho_ratio must be positive", LBM_ERR_ARG;
@@ -117,6 +118,8 @@ lbm::Params derive(const lbm_domain &d, const lbm_params &p) {
     k.gy = (float)p.gravity[1];
     k.gz = (float)p.gravity[2];
     k.rho_ref = (float)p.rho_ref;
+    k.phi_lo = p.clamp_phi ? 0.0f : -INFINITY;
+    k.phi_hi = p.clamp_phi ? 1.0f : INFINITY;
     return k;
 }
 

@@ -87,6 +87,7 @@ struct Params {
     float kappa;        // 3 sigma xi / 2
     float inv_xi;
     float gx, gy, gz, rho_ref;
+    float phi_lo, phi_hi;  // phi is clamped to [phi_lo, phi_hi] inside rho and tau
 };
 
 // Per-thread geometry: neighbour offsets along each axis (periodic wrap, or
@@ -162,23 +163,39 @@ __device__ __forceinline__ void gather_phi(const float *__restrict__ phi, const 
             for (int dx = -1; dx <= 1; ++dx) nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = __ldg(phi + nbr(C, dx, dy, dz));
 }
 
+// Error-free addition (Knuth's TwoSum): s + e == a + b exactly.
+struct DFloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum_acc(DFloat &acc, float b) {
+    const float s = acc.hi + b;
+    const float bb = s - acc.hi;
+    const float err = (acc.hi - (s - bb)) + (b - bb);
+    acc.hi = s;
+    acc.lo += err;
+}
+
 template <int Q>
 __device__ __forceinline__ float nb_at(const float nb[27], int i) {
     const V3 e = vel<Q>(i);
     return nb[(e.z + 1) * 9 + (e.y + 1) * 3 + (e.x + 1)];
 }
 
-// eq:grad: grad phi = (1/c_s^2) sum_i w_i e_i phi(x + e_i).
+// eq:grad: grad phi = (1/c_s^2) sum_i w_i e_i phi(x + e_i), summed over
+// opposite pairs as w_i e_i (phi(x + e_i) - phi(x - e_i)): the same sum, but each
+// difference of neighbouring values is exact in FP32 and a symmetric
+// neighbourhood gives exactly zero.
 template <int Q>
 __device__ __forceinline__ void stencil_grad(const float nb[27], float &gx, float &gy, float &gz) {
     float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
+    for (int i = 1; i < Q; i += 2) {  // i + 1 is the opposite of i
         const V3 e = vel<Q>(i);
-        const float v = wgt<Q>(i) * nb_at<Q>(nb, i);
-        if (e.x) sx += e.x > 0 ? v : -v;
-        if (e.y) sy += e.y > 0 ? v : -v;
-        if (e.z) sz += e.z > 0 ? v : -v;
+        const float d = wgt<Q>(i) * (nb_at<Q>(nb, i) - nb_at<Q>(nb, i + 1));
+        if (e.x) sx += e.x > 0 ? d : -d;
+        if (e.y) sy += e.y > 0 ? d : -d;
+        if (e.z) sz += e.z > 0 ? d : -d;
     }
     gx = 3.f * sx;
     gy = 3.f * sy;
@@ -191,7 +208,7 @@ __device__ __forceinline__ float stencil_lap(const float nb[27]) {
     const float c = nb[13];
     float s = 0.f;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) s += wgt<Q>(i) * (nb_at<Q>(nb, i) - c);
+    for (int i = 1; i < Q; i += 2) s += wgt<Q>(i) * ((nb_at<Q>(nb, i) - c) + (nb_at<Q>(nb, i + 1) - c));
     return 6.f * s;
 }
 
@@ -209,28 +226,31 @@ struct Hydro {
 
 template <int QG>
 __device__ __forceinline__ void hydro_macro(const Params &p, const float gv[QG], const float nb[27], Hydro<QG> &H) {
-    // moments of g
-    float ps = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f, myz = 0.f;
+    // moments of g over opposite pairs: s = g_i + g_opp(i) carries the even
+    // moments (p*, second moments), d = g_i - g_opp(i) the odd ones (j)
+    float ps = gv[0], jx = 0.f, jy = 0.f, jz = 0.f, mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f,
+          myz = 0.f;
 #pragma unroll
-    for (int i = 0; i < QG; ++i) {
+    for (int i = 1; i < QG; i += 2) {
         const V3 e = vel<QG>(i);
-        const float v = gv[i];
-        ps += v;
-        if (e.x) { jx += e.x > 0 ? v : -v; mxx += v; }
-        if (e.y) { jy += e.y > 0 ? v : -v; myy += v; }
-        if (e.z) { jz += e.z > 0 ? v : -v; mzz += v; }
-        if (e.x && e.y) mxy += (e.x * e.y > 0) ? v : -v;
-        if (e.x && e.z) mxz += (e.x * e.z > 0) ? v : -v;
-        if (e.y && e.z) myz += (e.y * e.z > 0) ? v : -v;
+        const float s = gv[i] + gv[i + 1], d = gv[i] - gv[i + 1];
+        ps += s;
+        if (e.x) { jx += e.x > 0 ? d : -d; mxx += s; }
+        if (e.y) { jy += e.y > 0 ? d : -d; myy += s; }
+        if (e.z) { jz += e.z > 0 ? d : -d; mzz += s; }
+        if (e.x && e.y) mxy += (e.x * e.y > 0) ? s : -s;
+        if (e.x && e.z) mxz += (e.x * e.z > 0) ? s : -s;
+        if (e.y && e.z) myz += (e.y * e.z > 0) ? s : -s;
     }
     const float phi = nb[13];
     float gpx, gpy, gpz;
     stencil_grad<QG>(nb, gpx, gpy, gpz);
     const float lap = stencil_lap<QG>(nb);
 
-    const float rho = p.rho_L + phi * p.drho;  // eq:density
+    const float phim = fminf(fmaxf(phi, p.phi_lo), p.phi_hi);
+    const float rho = p.rho_L + phim * p.drho;  // eq:density
     const float hir = 0.5f / rho;
-    const float tau = p.tau_L + phi * p.dtau;
+    const float tau = p.tau_L + phim * p.dtau;
     const float s_nu = 1.0f / (tau + 0.5f);
     const float grx = p.drho * gpx, gry = p.drho * gpy, grz = p.drho * gpz;
 
@@ -302,17 +322,20 @@ __device__ __forceinline__ HydroPost<QG> hydro_post(const Hydro<QG> &H) {
     return P;
 }
 
+// Even and odd parts of g*_i for a direction i of an opposite pair:
+// g*_i = E + O, g*_opp(i) = E - O.
 template <int QG>
-__device__ __forceinline__ float hydro_gstar(const HydroPost<QG> &P, int i) {
+__device__ __forceinline__ void hydro_gstar_pair(const HydroPost<QG> &P, int i, float &E, float &O) {
     const V3 e = vel<QG>(i);
-    float s = P.m0 - P.tr3;
-    if (e.x) s += (e.x > 0 ? P.m1x : -P.m1x) + P.bxx;
-    if (e.y) s += (e.y > 0 ? P.m1y : -P.m1y) + P.byy;
-    if (e.z) s += (e.z > 0 ? P.m1z : -P.m1z) + P.bzz;
-    if (e.x && e.y) s += (e.x * e.y > 0) ? P.bxy : -P.bxy;
-    if (e.x && e.z) s += (e.x * e.z > 0) ? P.bxz : -P.bxz;
-    if (e.y && e.z) s += (e.y * e.z > 0) ? P.byz : -P.byz;
-    return wgt<QG>(i) * s;
+    float ev = P.m0 - P.tr3, od = 0.f;
+    if (e.x) { od += e.x > 0 ? P.m1x : -P.m1x; ev += P.bxx; }
+    if (e.y) { od += e.y > 0 ? P.m1y : -P.m1y; ev += P.byy; }
+    if (e.z) { od += e.z > 0 ? P.m1z : -P.m1z; ev += P.bzz; }
+    if (e.x && e.y) ev += (e.x * e.y > 0) ? P.bxy : -P.bxy;
+    if (e.x && e.z) ev += (e.x * e.z > 0) ? P.bxz : -P.bxz;
+    if (e.y && e.z) ev += (e.y * e.z > 0) ? P.byz : -P.byz;
+    E = wgt<QG>(i) * ev;
+    O = wgt<QG>(i) * od;
 }
 
 }  // namespace lbm

@@ -46,8 +46,19 @@ __global__ void __launch_bounds__(256) fused_step_kernel(Params p, float *__rest
         Hydro<QG> Hd;
         hydro_macro<QG>(p, gv, nb, Hd);
         const HydroPost<QG> P = hydro_post<QG>(Hd);
+        // the rest population takes the remainder of the zeroth moment, so that
+        // sum_i g*_i = p* holds to rounding (the FP32 weights do not sum to 1)
+        float gsum = 0.f;
 #pragma unroll
-        for (int i = 0; i < QG; ++i) g[pop_dst<QG, G_SW>(C, N, i)] = hydro_gstar<QG>(P, i);
+        for (int i = 1; i < QG; i += 2) {
+            float E, O;
+            hydro_gstar_pair<QG>(P, i, E, O);
+            const float a = E + O, b = E - O;
+            g[pop_dst<QG, G_SW>(C, N, i)] = a;
+            g[pop_dst<QG, G_SW>(C, N, i + 1)] = b;
+            gsum += a + b;
+        }
+        g[pop_dst<QG, G_SW>(C, N, 0)] = Hd.pstar - gsum;
         ux = Hd.ux;
         uy = Hd.uy;
         uz = Hd.uz;
@@ -55,9 +66,13 @@ __global__ void __launch_bounds__(256) fused_step_kernel(Params p, float *__rest
     }
 
     // ---- phase-field step k
-    float phik = 0.f;
+    // phi_k = sum_i h_i, accumulated without rounding loss (the collision
+    // below puts the remainder of this sum into the rest population, so any
+    // rounding here would be a per-cell mass error)
+    DFloat phis{hv[0], 0.f};
 #pragma unroll
-    for (int i = 0; i < 15; ++i) phik += hv[i];
+    for (int i = 1; i < 15; ++i) two_sum_acc(phis, hv[i]);
+    const float phik = phis.hi + phis.lo;
     phi_out[C.c] = phik;
     if (!(fabsf(phik) < 1e30f)) *flag = 1;
 
@@ -66,7 +81,8 @@ __global__ void __launch_bounds__(256) fused_step_kernel(Params p, float *__rest
     const float G2 = Gx * Gx + Gy * Gy + Gz * Gz;
     float nx = 0.f, ny = 0.f, nz = 0.f;
     if (G2 > 1e-24f) {
-        const float inv = rsqrtf(G2);
+        float inv = rsqrtf(G2);
+        inv = inv * (1.5f - 0.5f * G2 * inv * inv);  // one Newton step: no systematic bias in |n|
         nx = Gx * inv;
         ny = Gy * inv;
         nz = Gz * inv;
@@ -75,16 +91,33 @@ __global__ void __launch_bounds__(256) fused_step_kernel(Params p, float *__rest
     const float theta = (1.0f - 4.0f * pc * pc) * p.inv_xi;
     const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
     const float om = p.omega_phi, fc = 1.0f - 0.5f * om;
+    // h*_i = h_i + omega (h^eq_i - h_i - F_i/2) + F_i over opposite pairs, with
+    // h^eq = phi_k w (1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u) and F_i = theta w e.n.
+    // The non-equilibrium h^eq_i - h_i is formed as fma(phi_hi, w, -h_i) +
+    // phi_lo w + phi w (velocity terms), so it carries no rounding of the large
+    // product phi w; the rest population takes the remainder so that
+    // sum_i h*_i = phi_k holds to the rounding of one store.
+    DFloat hsum{0.f, 0.f};
 #pragma unroll
-    for (int i = 0; i < 15; ++i) {
+    for (int i = 1; i < 15; i += 2) {
         const V3 e = vel<15>(i);
         const float w = wgt<15>(i);
         const float eu = e.x * ux + e.y * uy + e.z * uz;
         const float en = e.x * nx + e.y * ny + e.z * nz;
-        const float heq = phik * w * (1.0f + 3.0f * eu + 4.5f * eu * eu - uu);
-        const float F = theta * w * en;
-        h[pop_dst<15, H_SW>(C, N, i)] = hv[i] + om * (heq - hv[i]) + fc * F;
+        const float pw = phik * w;
+        const float x_even = pw * (4.5f * eu * eu - uu) + phis.lo * w;
+        const float x_odd = pw * 3.0f * eu;
+        const float F = fc * (theta * w * en);
+        const float neq_a = fmaf(phis.hi, w, -hv[i]) + (x_even + x_odd);
+        const float neq_b = fmaf(phis.hi, w, -hv[i + 1]) + (x_even - x_odd);
+        const float a = hv[i] + fmaf(om, neq_a, F);
+        const float b = hv[i + 1] + fmaf(om, neq_b, -F);
+        h[pop_dst<15, H_SW>(C, N, i)] = a;
+        h[pop_dst<15, H_SW>(C, N, i + 1)] = b;
+        two_sum_acc(hsum, a);
+        two_sum_acc(hsum, b);
     }
+    h[pop_dst<15, H_SW>(C, N, 0)] = (phis.hi - hsum.hi) + (phis.lo - hsum.lo);
 }
 
 template <int QG, bool G_SW, bool H_SW, bool HYDRO>

@@ -35,7 +35,7 @@ class lbm_params(ctypes.Structure):
     _fields_ = [("rho_H", ctypes.c_double), ("rho_ratio", ctypes.c_double), ("nu_H", ctypes.c_double),
                 ("mu_ratio", ctypes.c_double), ("sigma", ctypes.c_double), ("xi", ctypes.c_double),
                 ("mobility", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("rho_ref", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("clamp_phi", ctypes.c_int)]
 
 
 class LBMError(RuntimeError):
@@ -109,13 +109,13 @@ def make_domain(nx, ny, nz, wall=(0, 0, 0), q_hydro=27, q_phase=15) -> lbm_domai
 
 
 def make_params(rho_H=1.0, rho_ratio=1000.0, nu_H=0.01, mu_ratio=100.0, sigma=1e-4, xi=5.0, mobility=0.02,
-                gravity=(0.0, 0.0, 0.0), rho_ref=0.0, precision=LBM_PRECISION_FP32) -> lbm_params:
+                gravity=(0.0, 0.0, 0.0), rho_ref=0.0, precision=LBM_PRECISION_FP32, clamp_phi=0) -> lbm_params:
     p = lbm_params()
     p.rho_H, p.rho_ratio, p.nu_H, p.mu_ratio = float(rho_H), float(rho_ratio), float(nu_H), float(mu_ratio)
     p.sigma, p.xi, p.mobility = float(sigma), float(xi), float(mobility)
     for a in range(3):
         p.gravity[a] = float(gravity[a])
-    p.rho_ref, p.precision = float(rho_ref), int(precision)
+    p.rho_ref, p.precision, p.clamp_phi = float(rho_ref), int(precision), int(clamp_phi)
     return p
 
 
@@ -123,7 +123,7 @@ def from_problem(prob):
     """(lbm_domain, lbm_params) of a ``workloads.Problem``-like object."""
     d = make_domain(prob.nx, prob.ny, prob.nz, prob.wall, prob.q_hydro)
     p = make_params(prob.rho_H, prob.rho_ratio, prob.nu_H, prob.mu_ratio, prob.sigma, prob.xi, prob.mobility,
-                    prob.gravity, prob.rho_ref)
+                    prob.gravity, prob.rho_ref, clamp_phi=int(getattr(prob, "clamp_phi", 0)))
     return d, p
 
 

@@ -1,0 +1,107 @@
+"""Parity at the benchmark's full size, in the benchmark's launch configuration.
+
+The 512^3 roofline workload (D3Q15 + D3Q27, 400 bubbles) is advanced on the GPU
+through the C ABI.  For sampled cells, the one-step update is recomputed by the
+FP64 oracle: the new h, g and phi at a cell depend only on the state within
+distance 2 (streaming from x - e_i, whose collision reads phi at x - e_i + e_j),
+so the oracle steps a 5^3 periodic patch cut around the cell and its centre is
+compared with the GPU.  Global properties (mass conservation, finiteness) are
+checked on the whole field.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2012_06144_gb300 import lbm
+
+    return lbm
+
+
+def patch(arr, z, y, x, r=2):
+    """(..., 2r+1, 2r+1, 2r+1) periodic cut of a device tensor around (z, y, x), to numpy."""
+    import torch
+
+    nz, ny, nx = arr.shape[-3:]
+    iz = torch.tensor([(z + d) % nz for d in range(-r, r + 1)], device=arr.device)
+    iy = torch.tensor([(y + d) % ny for d in range(-r, r + 1)], device=arr.device)
+    ix = torch.tensor([(x + d) % nx for d in range(-r, r + 1)], device=arr.device)
+    out = arr.index_select(-3, iz).index_select(-2, iy).index_select(-1, ix)
+    return out.double().cpu().numpy()
+
+
+def check_sampled_step(lbm, orc, sim, prob, cells):
+    """One GPU step from the current state vs the oracle on 5^3 patches."""
+    h0, g0, phi0 = sim.get_state(on_device=True)
+    sim.step(1)
+    h1, g1, phi1 = sim.get_state(on_device=True)
+    sub = W.Problem(5, 5, 5, wall=(0, 0, 0), q_hydro=prob.q_hydro, rho_H=prob.rho_H, rho_ratio=prob.rho_ratio,
+                    nu_H=prob.nu_H, mu_ratio=prob.mu_ratio, sigma=prob.sigma, xi=prob.xi, mobility=prob.mobility,
+                    gravity=prob.gravity, rho_ref=prob.rho_ref, clamp_phi=prob.clamp_phi)
+    p = orc.make_problem(sub)
+    worst = 0.0
+    for z, y, x in cells:
+        hp, gp, fp = patch(h0, z, y, x), patch(g0, z, y, x), patch(phi0, z, y, x)
+        g_next, u = orc.hydro_step(p, gp, fp)
+        h_next, phi_next = orc.phase_step(p, hp, fp, u)
+        got_h = h1[:, z, y, x].double().cpu().numpy()
+        got_g = g1[:, z, y, x].double().cpu().numpy()
+        got_phi = float(phi1[z, y, x])
+        e_h = np.abs(got_h - h_next[:, 2, 2, 2]).max() / max(np.abs(h_next[:, 2, 2, 2]).max(), 1e-3)
+        e_g = np.abs(got_g - g_next[:, 2, 2, 2]).max() / max(np.abs(g_next[:, 2, 2, 2]).max(), 1e-6)
+        e_p = abs(got_phi - phi_next[2, 2, 2]) / max(abs(phi_next[2, 2, 2]), 1e-3)
+        worst = max(worst, e_h, e_g, e_p)
+        assert e_h <= TOL and e_g <= TOL and e_p <= TOL, (z, y, x, e_h, e_g, e_p)
+    return worst
+
+
+def test_roofline_512_sampled_one_step_parity(lbm, orc):
+    import torch
+
+    prob, phi0, bubbles = W.roofline()
+    sim = lbm.Simulation.from_problem(prob)
+    sim.init_phase(torch.from_numpy(phi0).cuda())
+    rng = np.random.default_rng(6144)
+    n = prob.nx
+    cells = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(48)]
+    # cells on the interfaces of a few bubbles, and on the box faces (periodic wrap)
+    for cx, cy, cz, r in bubbles[:16]:
+        cells.append((int(cz) % n, int(cy) % n, int(cx + r) % n))
+    cells += [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (n - 1, 3, 0)]
+    for warm in (0, 2):  # both in-place layouts of each lattice
+        sim.step(warm)
+        check_sampled_step(lbm, orc, sim, prob, cells)
+    sim.synchronize()
+    del sim
+    torch.cuda.empty_cache()
+
+
+def test_roofline_512_mass_and_finiteness(lbm):
+    import torch
+
+    prob, phi0, _ = W.roofline()
+    sim = lbm.Simulation.from_problem(prob)
+    sim.init_phase(torch.from_numpy(phi0).cuda())
+    m0 = sim.reduce()["mass"]
+    sim.step(50)
+    sim.synchronize()
+    d = sim.reduce()
+    assert np.isfinite(list(d.values())).all()
+    assert abs(d["mass"] - m0) <= 1e-6 * m0
+    assert d["max_u"] < 0.1
+    del sim
+    torch.cuda.empty_cache()

@@ -33,6 +33,22 @@ def rel_linf(a, b, floor=0.0):
     return float(np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), floor))
 
 
+def storage_floor(orc, prob, phi0, steps):
+    """The FP64 oracle's own deviation when its state is rounded to float32 after
+    every step (FP32 storage with exact arithmetic), per field (phi, u, p)."""
+    p = orc.make_problem(prob)
+    a, b = orc.State(p, phi0), orc.State(p, phi0)
+    for _ in range(steps):
+        a.run(1)
+        b.run(1)
+        b.h = b.h.astype(np.float32).astype(np.float64)
+        b.g = b.g.astype(np.float32).astype(np.float64)
+        b.phi_prev = b.phi_prev.astype(np.float32).astype(np.float64)
+    ref = a.fields()
+    floor = [rel_linf(x, y, 1e-6 if k == 1 else 0.0) for k, (x, y) in enumerate(zip(b.fields(), ref))]
+    return ref, floor
+
+
 def oracle_one_step(orc, prob, h, g, phi):
     """Oracle from the library's state (g^t, h^{t+1}, phi^t): hydro(t) then phase(t+1)."""
     p = orc.make_problem(prob)
@@ -88,6 +104,24 @@ def test_one_step_from_random_state(lbm, orc, nx, ny, nz, wall, q):
     assert rel_linf(g1, rg) <= TOL
 
 
+@pytest.mark.parametrize("nx,ny,nz,wall,q", CASES)
+def test_two_steps_from_random_state(lbm, orc, nx, ny, nz, wall, q):
+    """Covers the second in-place layout of both lattices (g swapped, h natural)."""
+    prob = W.Problem(nx, ny, nz, wall=wall, q_hydro=q, rho_ratio=100.0, mu_ratio=30.0, sigma=1e-3, xi=3.0,
+                     mobility=0.03, gravity=(1e-5, -2e-5, 3e-6), rho_ref=0.4)
+    h, g, phi = W.random_state(prob, seed=nx * 1000 + ny * 10 + nz + 7)
+    sim = lbm.Simulation.from_problem(prob)
+    sim.set_state(h, g, phi)
+    sim.step(2)
+    sim.synchronize()
+    h2, g2, phi2 = sim.get_state()
+    rh, rg, rphi = oracle_one_step(orc, prob, h, g, phi)
+    rh, rg, rphi = oracle_one_step(orc, prob, rh, rg, rphi)
+    assert rel_linf(phi2, rphi) <= TOL
+    assert rel_linf(h2, rh) <= TOL
+    assert rel_linf(g2, rg) <= TOL
+
+
 @pytest.mark.parametrize("steps", [0, 1, 2, 5])
 def test_state_roundtrip_each_parity(lbm, steps):
     """set_state followed by get_state returns the input exactly, whatever the
@@ -121,18 +155,21 @@ def test_split_steps_bitwise(lbm):
 
 
 def test_rising_bubble_walls(lbm, orc):
-    """Walled box, D3Q27, gravity and buoyancy: 150 steps against the oracle."""
-    prob, phi0 = W.rising_bubble(24, 48, 20, D=12.0, t_ref=300.0)
+    """Walled box, D3Q27, gravity, buoyancy and the phi clamp (Eo 10, Mo 1e-3,
+    t_ref 1000): 150 steps against the oracle.  The start from rest drives a
+    transient that amplifies rounding, so the bound is max(1e-5, 2 x the error
+    that FP32 storage alone causes in the oracle on the same case)."""
+    prob, phi0 = W.rising_bubble(24, 48, 20, D=12.0, t_ref=1000.0)
     sim = lbm.Simulation.from_problem(prob)
     sim.init_phase(phi0)
     sim.step(150)
     sim.synchronize()
     phi, u, p = sim.fields(on_device=False)
-    ref = orc.State(orc.make_problem(prob), phi0).run(150)
-    rphi, ru, rp = ref.fields()
-    assert rel_linf(phi, rphi) <= TOL
-    assert rel_linf(u, ru, 1e-6) <= TOL
-    assert rel_linf(p, rp) <= TOL
+    (rphi, ru, rp), floor = storage_floor(orc, prob, phi0, 150)
+    tol = [max(TOL, 2 * f) for f in floor]
+    assert rel_linf(phi, rphi) <= tol[0]
+    assert rel_linf(u, ru, 1e-6) <= tol[1]
+    assert rel_linf(p, rp) <= tol[2]
 
 
 def test_host_and_device_outputs_agree(lbm):
@@ -153,7 +190,7 @@ def test_reduce_matches_fields(lbm):
     sim.step(30)
     phi, u, p = (t.cpu().numpy().astype(np.float64) for t in sim.fields())
     d = sim.reduce()
-    rho = prob.rho_L + phi * (prob.rho_H - prob.rho_L)
+    rho = prob.rho_L + np.clip(phi, 0, 1) * (prob.rho_H - prob.rho_L)  # the workload clamps phi in rho
     lf = 1 - phi
     z, y, x = np.meshgrid(np.arange(16) + .5, np.arange(32) + .5, np.arange(16) + .5, indexing="ij")
     assert d["mass"] == pytest.approx(phi.sum(), rel=1e-9)

@@ -52,6 +52,7 @@ class Problem:
     mobility: float = 0.02
     gravity: tuple = (0.0, 0.0, 0.0)
     rho_ref: float = 1.0
+    clamp_phi: int = 0  # 1: phi clamped to [0, 1] inside rho and tau
 
     @property
     def rho_L(self) -> float:
@@ -206,7 +207,8 @@ def rising_bubble(nx: int = 128, ny: int = 512, nz: int = 128, D: float = 32.0, 
                   Eo: float = 10.0, Mo: float = 1e-3, t_ref: float = 2000.0, q_hydro: int = 27):
     g, sigma, nu_H = _bubble_params(D, Eo, Mo, t_ref)
     prob = Problem(nx, ny, nz, wall=(1, 1, 1), q_hydro=q_hydro, rho_H=1.0, rho_ratio=1000.0, nu_H=nu_H,
-                   mu_ratio=100.0, sigma=sigma, xi=5.0, mobility=0.04, gravity=(0.0, -g, 0.0), rho_ref=1.0)
+                   mu_ratio=100.0, sigma=sigma, xi=5.0, mobility=0.04, gravity=(0.0, -g, 0.0), rho_ref=1.0,
+                   clamp_phi=1)
     if centre is None:
         centre = (nx / 2, 2 * D, nz / 2)
     phi0 = sphere_phi(prob, centre, D / 2, heavy_inside=False)
@@ -221,7 +223,7 @@ def roofline(n: int = 512, count: int = 400, dmin: float = 16.0, dmax: float = 3
     sigma, Eo, D_ref = 1e-4, 10.0, 24.0
     g = Eo * sigma / (1.0 * D_ref * D_ref)
     prob = Problem(n, n, n, wall=(0, 0, 0), q_hydro=27, rho_H=1.0, rho_ratio=1000.0, nu_H=0.01,
-                   mu_ratio=100.0, sigma=sigma, xi=5.0, mobility=0.02, gravity=(0.0, -g, 0.0))
+                   mu_ratio=100.0, sigma=sigma, xi=5.0, mobility=0.02, gravity=(0.0, -g, 0.0), clamp_phi=1)
     bubbles = place_bubbles(prob, count, dmin, dmax, seed)
     phi0 = many_bubbles_phi(prob, bubbles).astype(np.float32)
     # buoyancy reference: the mean density, so a periodic gravity axis carries no net force
