@@ -50,10 +50,11 @@ def env_int(name, default):
         return default
 
 
-def workload(name: str):
+def workload(name: str, size: int = 512):
     if name == "roofline":
-        prob, phi0, bubbles = W.roofline()
-        desc = ("roofline: 512^3 triply periodic, D3Q15+D3Q27, FP32, 400 bubbles D~U[16,32] seed 6144, "
+        count = max(1, round(400 * (size / 512) ** 3))
+        prob, phi0, bubbles = W.roofline(n=size, count=count)
+        desc = (f"roofline: {size}^3 triply periodic, D3Q15+D3Q27, FP32, {count} bubbles D~U[16,32] seed 6144, "
                 "rho ratio 1000, mu ratio 100, sigma 1e-4, xi 5, M 0.02, gravity Eo=10 at D=24")
         return prob, phi0, desc
     if name == "rising_bubble":
@@ -213,6 +214,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="roofline", choices=["roofline", "rising_bubble"])
+    ap.add_argument("--size", type=int, default=512, help="edge of the roofline box (512 = the benchmark)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -243,7 +245,7 @@ def main():
     barrier()
     from paper_2012_06144_gb300 import lbm
 
-    prob, phi0, desc = workload(args.workload)
+    prob, phi0, desc = workload(args.workload, args.size)
     N = prob.ncells
     q = prob.q_hydro
     stream = torch.cuda.Stream()
@@ -318,7 +320,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "cells": N, "lattices": f"D3Q15+D3Q{q}", "storage": "fp32 in-place AA",
-                       "l2": "state 23.6 GB per GPU >> 129 MB L2, no flush needed",
+                       "l2": f"state {N * (15 + q + 2) * 4 / 1e9:.1f} GB per GPU >> 129 MB L2, no flush needed",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
             "gpu_launches": args.steps,

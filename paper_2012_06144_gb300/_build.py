@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import concurrent.futures
 import os
+import shlex
 import shutil
 import subprocess
 
@@ -26,6 +27,14 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-
                      "-I", CSRC, "-I", INCLUDE]
 
 
+def extra_flags() -> list:
+    """Additional nvcc flags from LBM_NVCC_FLAGS (tuning builds, e.g. -DLBM_MIN_BLOCKS=4)."""
+    return shlex.split(os.environ.get("LBM_NVCC_FLAGS", ""))
+
+
+STAMP = os.path.join(LIBDIR, "flags.txt")
+
+
 def nvcc() -> str:
     for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
@@ -39,7 +48,9 @@ def _inputs():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIBRARY):
+    if not os.path.exists(LIBRARY) or not os.path.exists(STAMP):
+        return False
+    if open(STAMP).read() != " ".join(extra_flags()):
         return False
     t = os.path.getmtime(LIBRARY)
     return all(os.path.getmtime(f) <= t for f in _inputs())
@@ -47,8 +58,8 @@ def up_to_date() -> bool:
 
 def _compile(src: str, ptxas_verbose: bool) -> tuple:
     obj = os.path.join(OBJDIR, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_verbose else []) + ["-c", os.path.join(CSRC, src),
-                                                                               "-o", obj]
+    cmd = [nvcc()] + NVCC_FLAGS + extra_flags() + (["-Xptxas", "-v"] if ptxas_verbose else []) + [
+        "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -72,6 +83,8 @@ def build(force: bool = False, ptxas_verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIBRARY)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(extra_flags()))
     return LIBRARY
 
 

@@ -14,35 +14,127 @@
 // The same stencil field phi^{k-1} serves both halves, so one pass reads
 // 15 h + q g + phi and writes 15 h + q g + phi per cell, and no velocity field is
 // stored.  The h lattice runs one time level ahead of g.
+//
+// Layout of the work: a block owns a 32 x 4 x 2 tile of cells (one warp = 32
+// consecutive x, so every population plane is read and written in full 128-byte
+// lines).  Each thread first issues the loads of its 15 + q populations, then the
+// block stages the phi tile with a one-cell halo in shared memory, so the stencil
+// values never occupy in-flight registers.  Population addresses are plane base
+// (a kernel parameter) + 4 (X[dx] + Y[dy] + Z[dz]), with the per-axis neighbour
+// offsets X, Y, Z computed once per thread (periodic wrap folded in); only blocks
+// that touch a walled face evaluate the bounce-back conditions.
 #include "lbm_internal.h"
 
 namespace lbm {
 
-template <int QG, bool G_SW, bool H_SW, bool HYDRO>
-__global__ void __launch_bounds__(256) fused_step_kernel(Params p, float *__restrict__ h, float *__restrict__ g,
-                                                         const float *__restrict__ phi_in,
-                                                         float *__restrict__ phi_out, int *__restrict__ flag) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= p.nx || y >= p.ny) return;
-    const Cell C = make_cell(p, x, y, z);
-    const long long N = p.N;
+#ifndef LBM_MIN_BLOCKS
+#define LBM_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for
+#endif
 
-    float nb[27];
-    gather_phi(phi_in, C, nb);
-    float gv[QG];
-    if (HYDRO) {
-#pragma unroll
-        for (int i = 0; i < QG; ++i) gv[i] = g[pop_src<QG, G_SW>(C, N, i)];
+constexpr int TX = 32, TY = 4, TZ = 2;
+constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
+
+struct Planes {
+    float *h[15];
+    float *g[27];
+};
+
+// Per-thread neighbour offsets: element index of (x+dx, y+dy, z+dz) is
+// X[dx+1] + Y[dy+1] + Z[dz+1] (X includes the cell's own index).
+struct Nb3 {
+    int X[3], Y[3], Z[3];
+    int lo, hi;  // walled faces touched by this cell (bit a: axis a)
+};
+
+__device__ __forceinline__ int nidx(const Nb3 &n, int dx, int dy, int dz) {
+    return n.X[dx + 1] + n.Y[dy + 1] + n.Z[dz + 1];
+}
+
+__device__ __forceinline__ bool leaves3(const Nb3 &n, V3 e, int sign) {
+    const int ex = e.x * sign, ey = e.y * sign, ez = e.z * sign;
+    return (ex > 0 && (n.hi & 1)) || (ex < 0 && (n.lo & 1)) || (ey > 0 && (n.hi & 2)) || (ey < 0 && (n.lo & 2)) ||
+           (ez > 0 && (n.hi & 4)) || (ez < 0 && (n.lo & 4));
+}
+
+// pre-collision f_i(x) of a lattice in the AA layout (see lbm_device.cuh)
+template <int Q, bool SW, bool EDGE>
+__device__ __forceinline__ float pop_load(float *const *pl, const Nb3 &n, int i) {
+    if (!SW) return pl[i][n.X[1]];
+    const V3 e = vel<Q>(i);
+    if (EDGE && leaves3(n, e, -1)) return pl[i][n.X[1]];
+    return pl[opp(i)][nidx(n, -e.x, -e.y, -e.z)];
+}
+
+template <int Q, bool SW, bool EDGE>
+__device__ __forceinline__ void pop_store(float *const *pl, const Nb3 &n, int i, float v) {
+    if (!SW) {
+        pl[opp(i)][n.X[1]] = v;
+        return;
     }
-    float hv[15];
-#pragma unroll
-    for (int i = 0; i < 15; ++i) hv[i] = h[pop_src<15, H_SW>(C, N, i)];
+    const V3 e = vel<Q>(i);
+    if (EDGE && leaves3(n, e, +1)) {
+        pl[opp(i)][n.X[1]] = v;
+        return;
+    }
+    pl[i][nidx(n, e.x, e.y, e.z)] = v;
+}
 
-    // ---- hydrodynamic step k-1
+template <int Q>
+__device__ __forceinline__ float tile_at(const float (*t)[HY][HX], int tx, int ty, int tz, int i) {
+    const V3 e = vel<Q>(i);
+    return t[tz + 1 + e.z][ty + 1 + e.y][tx + 1 + e.x];
+}
+
+template <int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE>
+__device__ __forceinline__ void cell_update(const Params &p, const Planes &pl, const Nb3 &n, bool active,
+                                            const float *__restrict__ phi_in, float (*tile)[HY][HX],
+                                            float *__restrict__ phi_out, int *__restrict__ flag) {
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+
+    // ---- issue the population loads first
+    float gv[QG], hv[15];
+    if (active) {
+        if (HYDRO) {
+#pragma unroll
+            for (int i = 0; i < QG; ++i) gv[i] = pop_load<QG, G_SW, EDGE>(pl.g, n, i);
+        }
+#pragma unroll
+        for (int i = 0; i < 15; ++i) hv[i] = pop_load<15, H_SW, EDGE>(pl.h, n, i);
+    }
+
+    // ---- stage phi^{k-1} with a one-cell halo (wrap on periodic axes, mirror at walls)
+    {
+        const int x0 = blockIdx.x * TX - 1, y0 = blockIdx.y * TY - 1, z0 = blockIdx.z * TZ - 1;
+        const int tid = tx + TX * (ty + TY * tz);
+        const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
+        for (int k = tid; k < HX * HY * HZ; k += TX * TY * TZ) {
+            const int kz = k / (HX * HY), r = k - kz * (HX * HY);
+            const int ky = r / HX, kx = r - ky * HX;
+            const int gx = wrap_or_clamp(x0 + kx, p.nx, wx);
+            const int gy = wrap_or_clamp(y0 + ky, p.ny, wy);
+            const int gz = wrap_or_clamp(z0 + kz, p.nz, wz);
+            // coordinates beyond a ragged box end are clamped into the box; those
+            // halo entries only feed threads that are inactive
+            const int cx = min(gx, p.nx - 1), cy = min(gy, p.ny - 1), cz = min(gz, p.nz - 1);
+            tile[kz][ky][kx] = __ldg(phi_in + cx + p.nx * (cy + p.ny * cz));
+        }
+    }
+    __syncthreads();
+    if (!active) return;
+
+    const float phic = tile[tz + 1][ty + 1][tx + 1];
     float ux = 0.f, uy = 0.f, uz = 0.f;
+
+    // ---- hydrodynamic step k-1 (Section 3.2)
     if (HYDRO) {
+        float nb[27];
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx)
+                    nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
         Hydro<QG> Hd;
         hydro_macro<QG>(p, gv, nb, Hd);
         const HydroPost<QG> P = hydro_post<QG>(Hd);
@@ -54,30 +146,41 @@ __global__ void __launch_bounds__(256) fused_step_kernel(Params p, float *__rest
             float E, O;
             hydro_gstar_pair<QG>(P, i, E, O);
             const float a = E + O, b = E - O;
-            g[pop_dst<QG, G_SW>(C, N, i)] = a;
-            g[pop_dst<QG, G_SW>(C, N, i + 1)] = b;
+            pop_store<QG, G_SW, EDGE>(pl.g, n, i, a);
+            pop_store<QG, G_SW, EDGE>(pl.g, n, i + 1, b);
             gsum += a + b;
         }
-        g[pop_dst<QG, G_SW>(C, N, 0)] = Hd.pstar - gsum;
+        pop_store<QG, G_SW, EDGE>(pl.g, n, 0, Hd.pstar - gsum);
         ux = Hd.ux;
         uy = Hd.uy;
         uz = Hd.uz;
         if (!(fabsf(Hd.pstar) < 1e30f)) *flag = 1;
     }
 
-    // ---- phase-field step k
-    // phi_k = sum_i h_i, accumulated without rounding loss (the collision
-    // below puts the remainder of this sum into the rest population, so any
-    // rounding here would be a per-cell mass error)
+    // ---- phase-field step k (Section 3.1)
+    // phi_k = sum_i h_i, accumulated without rounding loss (the collision below
+    // puts the remainder of this sum into the rest population, so any rounding
+    // here would be a per-cell mass error)
     DFloat phis{hv[0], 0.f};
 #pragma unroll
     for (int i = 1; i < 15; ++i) two_sum_acc(phis, hv[i]);
     const float phik = phis.hi + phis.lo;
-    phi_out[C.c] = phik;
+    phi_out[n.X[1]] = phik;
     if (!(fabsf(phik) < 1e30f)) *flag = 1;
 
-    float Gx, Gy, Gz;
-    stencil_grad<15>(nb, Gx, Gy, Gz);
+    // interface normal from eq:grad with D3Q15 weights, over opposite pairs
+    float Gx = 0.f, Gy = 0.f, Gz = 0.f;
+#pragma unroll
+    for (int i = 1; i < 15; i += 2) {
+        const V3 e = vel<15>(i);
+        const float d = wgt<15>(i) * (tile_at<15>(tile, tx, ty, tz, i) - tile_at<15>(tile, tx, ty, tz, i + 1));
+        if (e.x) Gx += e.x > 0 ? d : -d;
+        if (e.y) Gy += e.y > 0 ? d : -d;
+        if (e.z) Gz += e.z > 0 ? d : -d;
+    }
+    Gx *= 3.f;
+    Gy *= 3.f;
+    Gz *= 3.f;
     const float G2 = Gx * Gx + Gy * Gy + Gz * Gz;
     float nx = 0.f, ny = 0.f, nz = 0.f;
     if (G2 > 1e-24f) {
@@ -87,7 +190,7 @@ __global__ void __launch_bounds__(256) fused_step_kernel(Params p, float *__rest
         ny = Gy * inv;
         nz = Gz * inv;
     }
-    const float pc = nb[13] - 0.5f;
+    const float pc = phic - 0.5f;
     const float theta = (1.0f - 4.0f * pc * pc) * p.inv_xi;
     const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
     const float om = p.omega_phi, fc = 1.0f - 0.5f * om;
@@ -112,36 +215,76 @@ __global__ void __launch_bounds__(256) fused_step_kernel(Params p, float *__rest
         const float neq_b = fmaf(phis.hi, w, -hv[i + 1]) + (x_even - x_odd);
         const float a = hv[i] + fmaf(om, neq_a, F);
         const float b = hv[i + 1] + fmaf(om, neq_b, -F);
-        h[pop_dst<15, H_SW>(C, N, i)] = a;
-        h[pop_dst<15, H_SW>(C, N, i + 1)] = b;
+        pop_store<15, H_SW, EDGE>(pl.h, n, i, a);
+        pop_store<15, H_SW, EDGE>(pl.h, n, i + 1, b);
         two_sum_acc(hsum, a);
         two_sum_acc(hsum, b);
     }
-    h[pop_dst<15, H_SW>(C, N, 0)] = (phis.hi - hsum.hi) + (phis.lo - hsum.lo);
+    pop_store<15, H_SW, EDGE>(pl.h, n, 0, (phis.hi - hsum.hi) + (phis.lo - hsum.lo));
 }
 
 template <int QG, bool G_SW, bool H_SW, bool HYDRO>
-static cudaError_t launch(const Params &p, float *h, float *g, const float *pi, float *po, int *flag,
+__global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
+    fused_step_kernel(Params p, Planes pl, const float *__restrict__ phi_in, float *__restrict__ phi_out,
+                      int *__restrict__ flag) {
+    __shared__ float tile[HZ][HY][HX];
+    const int x = blockIdx.x * TX + threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    const int z = blockIdx.z * TZ + threadIdx.z;
+    const bool active = x < p.nx && y < p.ny && z < p.nz;
+
+    const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
+    const int xc = min(x, p.nx - 1), yc = min(y, p.ny - 1), zc = min(z, p.nz - 1);
+    const int nxy = p.nx * p.ny;
+    Nb3 n;
+    const int c = xc + p.nx * yc + nxy * zc;
+    n.X[0] = c + wrap_or_clamp(xc - 1, p.nx, wx) - xc;
+    n.X[1] = c;
+    n.X[2] = c + wrap_or_clamp(xc + 1, p.nx, wx) - xc;
+    n.Y[0] = (wrap_or_clamp(yc - 1, p.ny, wy) - yc) * p.nx;
+    n.Y[1] = 0;
+    n.Y[2] = (wrap_or_clamp(yc + 1, p.ny, wy) - yc) * p.nx;
+    n.Z[0] = (wrap_or_clamp(zc - 1, p.nz, wz) - zc) * nxy;
+    n.Z[1] = 0;
+    n.Z[2] = (wrap_or_clamp(zc + 1, p.nz, wz) - zc) * nxy;
+    n.lo = (wx && xc == 0 ? 1 : 0) | (wy && yc == 0 ? 2 : 0) | (wz && zc == 0 ? 4 : 0);
+    n.hi = (wx && xc == p.nx - 1 ? 1 : 0) | (wy && yc == p.ny - 1 ? 2 : 0) | (wz && zc == p.nz - 1 ? 4 : 0);
+
+    // blocks that touch a walled face take the path with bounce-back checks
+    const bool edge = (wx && (blockIdx.x == 0 || (blockIdx.x + 1) * TX >= p.nx)) ||
+                      (wy && (blockIdx.y == 0 || (blockIdx.y + 1) * TY >= p.ny)) ||
+                      (wz && (blockIdx.z == 0 || (blockIdx.z + 1) * TZ >= p.nz));
+    if (edge)
+        cell_update<QG, G_SW, H_SW, HYDRO, true>(p, pl, n, active, phi_in, tile, phi_out, flag);
+    else
+        cell_update<QG, G_SW, H_SW, HYDRO, false>(p, pl, n, active, phi_in, tile, phi_out, flag);
+}
+
+template <int QG, bool G_SW, bool H_SW, bool HYDRO>
+static cudaError_t launch(const Params &p, const Planes &pl, const float *pi, float *po, int *flag,
                           cudaStream_t st) {
-    const dim3 block(32, 8, 1);
-    const dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, p.nz);
-    fused_step_kernel<QG, G_SW, H_SW, HYDRO><<<grid, block, 0, st>>>(p, h, g, pi, po, flag);
+    const dim3 block(TX, TY, TZ);
+    const dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + TZ - 1) / TZ);
+    fused_step_kernel<QG, G_SW, H_SW, HYDRO><<<grid, block, 0, st>>>(p, pl, pi, po, flag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step(const Params &p, int q_hydro, bool g_sw, bool h_sw, bool hydro, float *h, float *g,
                         const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
+    Planes pl;
+    for (int i = 0; i < 15; ++i) pl.h[i] = h + (size_t)i * p.N;
+    for (int i = 0; i < 27; ++i) pl.g[i] = i < q_hydro ? g + (size_t)i * p.N : nullptr;
     if (!hydro) {
         if (h_sw) return cudaErrorInvalidValue;  // the first phase step starts from natural h
-        return launch<19, false, false, false>(p, h, g, phi_in, phi_out, flag, st);
+        return launch<19, false, false, false>(p, pl, phi_in, phi_out, flag, st);
     }
     if (g_sw == h_sw) return cudaErrorInvalidValue;  // h runs one AA step ahead of g
     if (q_hydro == 19)
-        return g_sw ? launch<19, true, false, true>(p, h, g, phi_in, phi_out, flag, st)
-                    : launch<19, false, true, true>(p, h, g, phi_in, phi_out, flag, st);
+        return g_sw ? launch<19, true, false, true>(p, pl, phi_in, phi_out, flag, st)
+                    : launch<19, false, true, true>(p, pl, phi_in, phi_out, flag, st);
     if (q_hydro == 27)
-        return g_sw ? launch<27, true, false, true>(p, h, g, phi_in, phi_out, flag, st)
-                    : launch<27, false, true, true>(p, h, g, phi_in, phi_out, flag, st);
+        return g_sw ? launch<27, true, false, true>(p, pl, phi_in, phi_out, flag, st)
+                    : launch<27, false, true, true>(p, pl, phi_in, phi_out, flag, st);
     return cudaErrorInvalidValue;
 }
 
