@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) fields_kernel(Params p, const float *__re
 #pragma unroll
     for (int i = 0; i < QG; ++i) gv[i] = g[pop_src<QG, G_SW>(C, p.N, i)];
     Hydro<QG> H;
-    hydro_macro<QG>(p, gv, nb, H);
+    hydro_macro<QG>(p, gv, nb[13], stencil_sums(nb), H);
     if (out_phi) out_phi[C.c] = nb[13];
     if (ux) ux[C.c] = H.ux;
     if (uy) uy[C.c] = H.uy;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) reduce_partial_kernel(Params p, const flo
 #pragma unroll
         for (int i = 0; i < QG; ++i) gv[i] = g[pop_src<QG, G_SW>(C, p.N, i)];
         Hydro<QG> H;
-        hydro_macro<QG>(p, gv, nb, H);
+        hydro_macro<QG>(p, gv, nb[13], stencil_sums(nb), H);
         const double f = nb[13], lf = 1.0 - f, rho = H.rho;
         acc[0] += f;
         acc[1] += rho * H.ux;

@@ -163,53 +163,68 @@ __device__ __forceinline__ void gather_phi(const float *__restrict__ phi, const 
             for (int dx = -1; dx <= 1; ++dx) nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = __ldg(phi + nbr(C, dx, dy, dz));
 }
 
-// Error-free addition (Knuth's TwoSum): s + e == a + b exactly.
-struct DFloat {
-    float hi, lo;
-};
-
-__device__ __forceinline__ void two_sum_acc(DFloat &acc, float b) {
-    const float s = acc.hi + b;
-    const float bb = s - acc.hi;
-    const float err = (acc.hi - (s - bb)) + (b - bb);
-    acc.hi = s;
-    acc.lo += err;
-}
-
 template <int Q>
 __device__ __forceinline__ float nb_at(const float nb[27], int i) {
     const V3 e = vel<Q>(i);
     return nb[(e.z + 1) * 9 + (e.y + 1) * 3 + (e.x + 1)];
 }
 
-// eq:grad: grad phi = (1/c_s^2) sum_i w_i e_i phi(x + e_i), summed over
-// opposite pairs as w_i e_i (phi(x + e_i) - phi(x - e_i)): the same sum, but each
-// difference of neighbouring values is exact in FP32 and a symmetric
-// neighbourhood gives exactly zero.
-template <int Q>
-__device__ __forceinline__ void stencil_grad(const float nb[27], float &gx, float &gy, float &gz) {
-    float sx = 0.f, sy = 0.f, sz = 0.f;
+// Isotropic stencils eq:grad and eq:lap from the 3x3x3 neighbourhood.  The 26
+// differences d(e) = phi(x + e) - phi(x) are formed once (exact in FP32 for
+// neighbouring values) and grouped by opposite pairs and weight class (face,
+// edge, corner), so that
+//   grad phi = (1/c_s^2) sum_i w_i e_i phi(x + e_i) = 3 sum_class w_class D_class
+//   lap  phi = (2/c_s^2) sum_i w_i d(e_i)           = 6 sum_class w_class L_class
+// for D3Q15 (faces, corners), D3Q19 (faces, edges) and D3Q27 (all three) alike.
+// A symmetric neighbourhood gives a gradient of exactly zero.
+struct Stencil {
+    float D1[3], D2[3], D3[3];  // sum over the class of e_a (phi(x + e) - phi(x - e)), one rep. per pair
+    float L1, L2, L3;           // sum over the class of d(e) + d(-e)
+};
+
+__device__ __forceinline__ Stencil stencil_sums(const float nb[27]) {
+    Stencil S;
 #pragma unroll
-    for (int i = 1; i < Q; i += 2) {  // i + 1 is the opposite of i
-        const V3 e = vel<Q>(i);
-        const float d = wgt<Q>(i) * (nb_at<Q>(nb, i) - nb_at<Q>(nb, i + 1));
-        if (e.x) sx += e.x > 0 ? d : -d;
-        if (e.y) sy += e.y > 0 ? d : -d;
-        if (e.z) sz += e.z > 0 ? d : -d;
+    for (int a = 0; a < 3; ++a) S.D1[a] = S.D2[a] = S.D3[a] = 0.f;
+    S.L1 = S.L2 = S.L3 = 0.f;
+    const float c = nb[13];
+#pragma unroll
+    for (int i = 1; i < 27; i += 2) {  // i + 1 is the opposite of i
+        const V3 e = vel27(i);
+        const float vp = nb_at<27>(nb, i), vm = nb_at<27>(nb, i + 1);
+        const float D = vp - vm, L = (vp - c) + (vm - c);
+        const int cls = e.x * e.x + e.y * e.y + e.z * e.z;
+        float *Dc = cls == 1 ? S.D1 : (cls == 2 ? S.D2 : S.D3);
+        if (e.x) Dc[0] += e.x > 0 ? D : -D;
+        if (e.y) Dc[1] += e.y > 0 ? D : -D;
+        if (e.z) Dc[2] += e.z > 0 ? D : -D;
+        if (cls == 1) S.L1 += L;
+        else if (cls == 2) S.L2 += L;
+        else S.L3 += L;
     }
-    gx = 3.f * sx;
-    gy = 3.f * sy;
-    gz = 3.f * sz;
+    return S;
 }
 
-// eq:lap: lap phi = (2/c_s^2) sum_i w_i (phi(x + e_i) - phi(x)).
+// weight of a class (|e|^2 = 1, 2, 3) in lattice Q; 0 if the class is absent
 template <int Q>
-__device__ __forceinline__ float stencil_lap(const float nb[27]) {
-    const float c = nb[13];
-    float s = 0.f;
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) s += wgt<Q>(i) * ((nb_at<Q>(nb, i) - c) + (nb_at<Q>(nb, i + 1) - c));
-    return 6.f * s;
+__host__ __device__ constexpr float wclass(int cls) {
+    return Q == 15 ? (cls == 1 ? 1.0f / 9.0f : (cls == 3 ? 1.0f / 72.0f : 0.0f))
+         : Q == 19 ? (cls == 1 ? 1.0f / 18.0f : (cls == 2 ? 1.0f / 36.0f : 0.0f))
+                   : (cls == 1 ? 2.0f / 27.0f : (cls == 2 ? 1.0f / 54.0f : 1.0f / 216.0f));
+}
+
+template <int Q>
+__device__ __forceinline__ void stencil_grad(const Stencil &S, float &gx, float &gy, float &gz) {
+    constexpr float w1 = 3.f * wclass<Q>(1), w2 = 3.f * wclass<Q>(2), w3 = 3.f * wclass<Q>(3);
+    gx = w1 * S.D1[0] + (w2 != 0.f ? w2 * S.D2[0] : 0.f) + (w3 != 0.f ? w3 * S.D3[0] : 0.f);
+    gy = w1 * S.D1[1] + (w2 != 0.f ? w2 * S.D2[1] : 0.f) + (w3 != 0.f ? w3 * S.D3[1] : 0.f);
+    gz = w1 * S.D1[2] + (w2 != 0.f ? w2 * S.D2[2] : 0.f) + (w3 != 0.f ? w3 * S.D3[2] : 0.f);
+}
+
+template <int Q>
+__device__ __forceinline__ float stencil_lap(const Stencil &S) {
+    constexpr float w1 = 6.f * wclass<Q>(1), w2 = 6.f * wclass<Q>(2), w3 = 6.f * wclass<Q>(3);
+    return w1 * S.L1 + (w2 != 0.f ? w2 * S.L2 : 0.f) + (w3 != 0.f ? w3 * S.L3 : 0.f);
 }
 
 // Macroscopic quantities and forces of the hydrodynamic step at one cell
@@ -225,7 +240,8 @@ struct Hydro {
 };
 
 template <int QG>
-__device__ __forceinline__ void hydro_macro(const Params &p, const float gv[QG], const float nb[27], Hydro<QG> &H) {
+__device__ __forceinline__ void hydro_macro(const Params &p, const float gv[QG], float phi, const Stencil &S,
+                                            Hydro<QG> &H) {
     // moments of g over opposite pairs: s = g_i + g_opp(i) carries the even
     // moments (p*, second moments), d = g_i - g_opp(i) the odd ones (j)
     float ps = gv[0], jx = 0.f, jy = 0.f, jz = 0.f, mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f,
@@ -242,16 +258,15 @@ __device__ __forceinline__ void hydro_macro(const Params &p, const float gv[QG],
         if (e.x && e.z) mxz += (e.x * e.z > 0) ? s : -s;
         if (e.y && e.z) myz += (e.y * e.z > 0) ? s : -s;
     }
-    const float phi = nb[13];
     float gpx, gpy, gpz;
-    stencil_grad<QG>(nb, gpx, gpy, gpz);
-    const float lap = stencil_lap<QG>(nb);
+    stencil_grad<QG>(S, gpx, gpy, gpz);
+    const float lap = stencil_lap<QG>(S);
 
     const float phim = fminf(fmaxf(phi, p.phi_lo), p.phi_hi);
     const float rho = p.rho_L + phim * p.drho;  // eq:density
-    const float hir = 0.5f / rho;
+    const float hir = 0.5f * __frcp_rn(rho);
     const float tau = p.tau_L + phim * p.dtau;
-    const float s_nu = 1.0f / (tau + 0.5f);
+    const float s_nu = __frcp_rn(tau + 0.5f);
     const float grx = p.drho * gpx, gry = p.drho * gpy, grz = p.drho * gpz;
 
     // eq:chemPot, eq:surfaceTension

@@ -31,7 +31,17 @@ namespace lbm {
 #define LBM_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for
 #endif
 
-constexpr int TX = 32, TY = 4, TZ = 2;
+#ifndef LBM_TY
+#define LBM_TY 4
+#endif
+#ifndef LBM_TZ
+#define LBM_TZ 2
+#endif
+#ifndef LBM_STREAM_HINTS
+#define LBM_STREAM_HINTS 1  // 1: populations move with evict-first (.cs) loads and stores
+#endif
+
+constexpr int TX = 32, TY = LBM_TY, TZ = LBM_TZ;
 constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 
 struct Planes {
@@ -56,33 +66,43 @@ __device__ __forceinline__ bool leaves3(const Nb3 &n, V3 e, int sign) {
            (ez > 0 && (n.hi & 4)) || (ez < 0 && (n.lo & 4));
 }
 
+__device__ __forceinline__ float ld_pop(const float *a) {
+#if LBM_STREAM_HINTS
+    return __ldcs(a);
+#else
+    return *a;
+#endif
+}
+
+__device__ __forceinline__ void st_pop(float *a, float v) {
+#if LBM_STREAM_HINTS
+    __stcs(a, v);
+#else
+    *a = v;
+#endif
+}
+
 // pre-collision f_i(x) of a lattice in the AA layout (see lbm_device.cuh)
 template <int Q, bool SW, bool EDGE>
 __device__ __forceinline__ float pop_load(float *const *pl, const Nb3 &n, int i) {
-    if (!SW) return pl[i][n.X[1]];
+    if (!SW) return ld_pop(pl[i] + n.X[1]);
     const V3 e = vel<Q>(i);
-    if (EDGE && leaves3(n, e, -1)) return pl[i][n.X[1]];
-    return pl[opp(i)][nidx(n, -e.x, -e.y, -e.z)];
+    if (EDGE && leaves3(n, e, -1)) return ld_pop(pl[i] + n.X[1]);
+    return ld_pop(pl[opp(i)] + nidx(n, -e.x, -e.y, -e.z));
 }
 
 template <int Q, bool SW, bool EDGE>
 __device__ __forceinline__ void pop_store(float *const *pl, const Nb3 &n, int i, float v) {
     if (!SW) {
-        pl[opp(i)][n.X[1]] = v;
+        st_pop(pl[opp(i)] + n.X[1], v);
         return;
     }
     const V3 e = vel<Q>(i);
     if (EDGE && leaves3(n, e, +1)) {
-        pl[opp(i)][n.X[1]] = v;
+        st_pop(pl[opp(i)] + n.X[1], v);
         return;
     }
-    pl[i][nidx(n, e.x, e.y, e.z)] = v;
-}
-
-template <int Q>
-__device__ __forceinline__ float tile_at(const float (*t)[HY][HX], int tx, int ty, int tz, int i) {
-    const V3 e = vel<Q>(i);
-    return t[tz + 1 + e.z][ty + 1 + e.y][tx + 1 + e.x];
+    st_pop(pl[i] + nidx(n, e.x, e.y, e.z), v);
 }
 
 template <int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE>
@@ -122,21 +142,22 @@ __device__ __forceinline__ void cell_update(const Params &p, const Planes &pl, c
     __syncthreads();
     if (!active) return;
 
-    const float phic = tile[tz + 1][ty + 1][tx + 1];
+    float nb[27];
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx)
+                nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
+    const float phic = nb[13];
+    const Stencil S = stencil_sums(nb);
     float ux = 0.f, uy = 0.f, uz = 0.f;
 
     // ---- hydrodynamic step k-1 (Section 3.2)
     if (HYDRO) {
-        float nb[27];
-#pragma unroll
-        for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                for (int dx = -1; dx <= 1; ++dx)
-                    nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
         Hydro<QG> Hd;
-        hydro_macro<QG>(p, gv, nb, Hd);
+        hydro_macro<QG>(p, gv, phic, S, Hd);
         const HydroPost<QG> P = hydro_post<QG>(Hd);
         // the rest population takes the remainder of the zeroth moment, so that
         // sum_i g*_i = p* holds to rounding (the FP32 weights do not sum to 1)
@@ -158,29 +179,19 @@ __device__ __forceinline__ void cell_update(const Params &p, const Planes &pl, c
     }
 
     // ---- phase-field step k (Section 3.1)
-    // phi_k = sum_i h_i, accumulated without rounding loss (the collision below
-    // puts the remainder of this sum into the rest population, so any rounding
-    // here would be a per-cell mass error)
-    DFloat phis{hv[0], 0.f};
+    // phi_k = sum_i h_i (eq:updatePhaseField), summed as a tree over opposite pairs
+    float pr[8];
+    pr[0] = hv[0];
 #pragma unroll
-    for (int i = 1; i < 15; ++i) two_sum_acc(phis, hv[i]);
-    const float phik = phis.hi + phis.lo;
+    for (int j = 0; j < 7; ++j) pr[j + 1] = hv[2 * j + 1] + hv[2 * j + 2];
+    const float phik = ((pr[0] + pr[1]) + (pr[2] + pr[3])) + ((pr[4] + pr[5]) + (pr[6] + pr[7]));
     phi_out[n.X[1]] = phik;
     if (!(fabsf(phik) < 1e30f)) *flag = 1;
 
-    // interface normal from eq:grad with D3Q15 weights, over opposite pairs
-    float Gx = 0.f, Gy = 0.f, Gz = 0.f;
-#pragma unroll
-    for (int i = 1; i < 15; i += 2) {
-        const V3 e = vel<15>(i);
-        const float d = wgt<15>(i) * (tile_at<15>(tile, tx, ty, tz, i) - tile_at<15>(tile, tx, ty, tz, i + 1));
-        if (e.x) Gx += e.x > 0 ? d : -d;
-        if (e.y) Gy += e.y > 0 ? d : -d;
-        if (e.z) Gz += e.z > 0 ? d : -d;
-    }
-    Gx *= 3.f;
-    Gy *= 3.f;
-    Gz *= 3.f;
+    // interface normal from eq:grad with D3Q15 weights (the face and corner sums
+    // of the same neighbourhood)
+    float Gx, Gy, Gz;
+    stencil_grad<15>(S, Gx, Gy, Gz);
     const float G2 = Gx * Gx + Gy * Gy + Gz * Gz;
     float nx = 0.f, ny = 0.f, nz = 0.f;
     if (G2 > 1e-24f) {
@@ -196,11 +207,13 @@ __device__ __forceinline__ void cell_update(const Params &p, const Planes &pl, c
     const float om = p.omega_phi, fc = 1.0f - 0.5f * om;
     // h*_i = h_i + omega (h^eq_i - h_i - F_i/2) + F_i over opposite pairs, with
     // h^eq = phi_k w (1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u) and F_i = theta w e.n.
-    // The non-equilibrium h^eq_i - h_i is formed as fma(phi_hi, w, -h_i) +
-    // phi_lo w + phi w (velocity terms), so it carries no rounding of the large
-    // product phi w; the rest population takes the remainder so that
-    // sum_i h*_i = phi_k holds to the rounding of one store.
-    DFloat hsum{0.f, 0.f};
+    // The non-equilibrium h^eq_i - h_i is formed as fma(phi_k, w, -h_i) + phi_k w
+    // (velocity terms), so it carries no rounding of the large product phi w.
+    // The rest population takes h_0 - sum_{i>0} (h*_i - h_i): each increment is
+    // exact in FP32 (h*_i and h_i are close), so the stored populations sum to
+    // the incoming sum_i h_i up to the rounding of small increments, i.e. the
+    // cell's phase mass is kept.
+    float dsum = 0.f;
 #pragma unroll
     for (int i = 1; i < 15; i += 2) {
         const V3 e = vel<15>(i);
@@ -208,19 +221,18 @@ __device__ __forceinline__ void cell_update(const Params &p, const Planes &pl, c
         const float eu = e.x * ux + e.y * uy + e.z * uz;
         const float en = e.x * nx + e.y * ny + e.z * nz;
         const float pw = phik * w;
-        const float x_even = pw * (4.5f * eu * eu - uu) + phis.lo * w;
+        const float x_even = pw * (4.5f * eu * eu - uu);
         const float x_odd = pw * 3.0f * eu;
         const float F = fc * (theta * w * en);
-        const float neq_a = fmaf(phis.hi, w, -hv[i]) + (x_even + x_odd);
-        const float neq_b = fmaf(phis.hi, w, -hv[i + 1]) + (x_even - x_odd);
+        const float neq_a = fmaf(phik, w, -hv[i]) + (x_even + x_odd);
+        const float neq_b = fmaf(phik, w, -hv[i + 1]) + (x_even - x_odd);
         const float a = hv[i] + fmaf(om, neq_a, F);
         const float b = hv[i + 1] + fmaf(om, neq_b, -F);
         pop_store<15, H_SW, EDGE>(pl.h, n, i, a);
         pop_store<15, H_SW, EDGE>(pl.h, n, i + 1, b);
-        two_sum_acc(hsum, a);
-        two_sum_acc(hsum, b);
+        dsum += (a - hv[i]) + (b - hv[i + 1]);
     }
-    pop_store<15, H_SW, EDGE>(pl.h, n, 0, (phis.hi - hsum.hi) + (phis.lo - hsum.lo));
+    pop_store<15, H_SW, EDGE>(pl.h, n, 0, hv[0] - dsum);
 }
 
 template <int QG, bool G_SW, bool H_SW, bool HYDRO>
