@@ -155,11 +155,31 @@ lbm_status lbm_synchronize(lbm_t *s);
 int64_t lbm_steps_done(const lbm_t *s);
 
 /* Text of the last failure on this handle; with s == NULL, of the last failed
- * lbm_create on the calling thread. */
+ * call without a handle (lbm_workspace_size, lbm_create,
+ * lbm_reduce_state_noalloc) on the calling thread. */
 const char *lbm_last_error(const lbm_t *s);
 
 /* Releases the handle and, if the library allocated it, the workspace. */
 void lbm_destroy(lbm_t *s);
+
+/* The LBM_DIAG_* diagnostics of a state that the caller holds in device memory,
+ * computed without allocating any device memory.  The paper has no counterpart:
+ * this serves callers that cannot allocate at this point -- a host application
+ * whose memory pool already owns the GPU's free memory, or a time loop that must
+ * not take the synchronisation cudaMalloc/cudaFree can cause.
+ *   g, phi : device pointers to g^t (q_hydro planes, natural layout) and phi^t
+ *            (nx*ny*nz floats), e.g. as lbm_get_state(..., on_device = 1) returns;
+ *   out    : LBM_DIAG_COUNT doubles in host memory;
+ *   cuda_stream : stream to run on (NULL: legacy default); synchronised on return.
+ * Scratch space is a fixed array inside the library (about 786 KB per GPU, held
+ * until the process exits): boxes of more than 134,217,728 cells (512^3) are
+ * rejected with LBM_ERR_ARG.  The first call on a device looks up that array's
+ * device address, so make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (each call overwrites
+ * what it reads); calls that overlap on the GPU race on it, so the caller must
+ * serialise them. */
+lbm_status lbm_reduce_state_noalloc(const lbm_domain *dom, const lbm_params *prm, const float *g, const float *phi,
+                                    double *out, void *cuda_stream);
 
 #ifdef __cplusplus
 }

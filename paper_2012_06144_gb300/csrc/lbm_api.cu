@@ -153,6 +153,23 @@ cudaMemcpyKind kind_to_device(int on_device) { return on_device ? cudaMemcpyDevi
 
 }  // namespace
 
+namespace lbm {
+// Validation and derived parameters for entry points outside this file.
+lbm_status prepare_problem(const lbm_domain *dom, const lbm_params *prm, Params *out, std::string *why) {
+    std::string w;
+    const lbm_status st = validate(dom, prm, w);
+    if (st != LBM_OK) {
+        if (why) *why = w;
+        return st;
+    }
+    *out = derive(*dom, *prm);
+    return LBM_OK;
+}
+
+// Message returned by lbm_last_error(NULL) for a call without a handle.
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace lbm
+
 extern "C" {
 
 lbm_status lbm_workspace_size(const lbm_domain *dom, const lbm_params *prm, size_t *bytes) {

@@ -3,6 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
+#include "lbm.h"
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -32,5 +35,9 @@ constexpr int kReduceBlocks = 1024;
 constexpr int kDiagSlots = 12;
 cudaError_t launch_reduce(const Params &p, int q_hydro, bool g_swapped, const float *g, const float *phi,
                           double *scratch, double *out, cudaStream_t st);
+
+// Validates a problem and derives the kernel parameters (defined with the C ABI).
+lbm_status prepare_problem(const lbm_domain *dom, const lbm_params *prm, Params *out, std::string *why);
+void set_thread_error(const std::string &msg);
 
 }  // namespace lbm

@@ -63,6 +63,8 @@ _SIGNATURES = {
     "lbm_steps_done": ([_VP], ctypes.c_int64),
     "lbm_last_error": ([_VP], ctypes.c_char_p),
     "lbm_destroy": ([_VP], None),
+    "lbm_reduce_state_noalloc": ([ctypes.POINTER(lbm_domain), ctypes.POINTER(lbm_params), _FP, _FP, _DP, _VP],
+                                 ctypes.c_int),
 }
 
 
@@ -184,6 +186,15 @@ def lbm_last_error(h=None) -> str:
 
 def lbm_destroy(h):
     load().lbm_destroy(h)
+
+
+def lbm_reduce_state_noalloc(dom: lbm_domain, prm: lbm_params, g: int, phi: int, stream: int = 0) -> np.ndarray:
+    """Diagnostics of a device-resident state (g natural layout, phi) without any
+    device allocation by the library; see include/lbm.h."""
+    out = np.zeros(LBM_DIAG_COUNT)
+    _check(load().lbm_reduce_state_noalloc(ctypes.byref(dom), ctypes.byref(prm), g, phi, out.ctypes.data_as(_DP),
+                                           stream or None))
+    return out
 
 
 # ---- convenience wrapper: device memory and stream from PyTorch --------------------------------------
