@@ -105,51 +105,13 @@ __device__ __forceinline__ void pop_store(float *const *pl, const Nb3 &n, int i,
     st_pop(pl[i] + nidx(n, e.x, e.y, e.z), v);
 }
 
+// Collision of both lattices at one cell and the streaming stores, from the
+// pre-collision populations gv (g^{k-1}), hv (h^k) and the 3x3x3 neighbourhood nb
+// of phi^{k-1}.
 template <int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE>
-__device__ __forceinline__ void cell_update(const Params &p, const Planes &pl, const Nb3 &n, bool active,
-                                            const float *__restrict__ phi_in, float (*tile)[HY][HX],
-                                            float *__restrict__ phi_out, int *__restrict__ flag) {
-    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-
-    // ---- issue the population loads first
-    float gv[QG], hv[15];
-    if (active) {
-        if (HYDRO) {
-#pragma unroll
-            for (int i = 0; i < QG; ++i) gv[i] = pop_load<QG, G_SW, EDGE>(pl.g, n, i);
-        }
-#pragma unroll
-        for (int i = 0; i < 15; ++i) hv[i] = pop_load<15, H_SW, EDGE>(pl.h, n, i);
-    }
-
-    // ---- stage phi^{k-1} with a one-cell halo (wrap on periodic axes, mirror at walls)
-    {
-        const int x0 = blockIdx.x * TX - 1, y0 = blockIdx.y * TY - 1, z0 = blockIdx.z * TZ - 1;
-        const int tid = tx + TX * (ty + TY * tz);
-        const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
-        for (int k = tid; k < HX * HY * HZ; k += TX * TY * TZ) {
-            const int kz = k / (HX * HY), r = k - kz * (HX * HY);
-            const int ky = r / HX, kx = r - ky * HX;
-            const int gx = wrap_or_clamp(x0 + kx, p.nx, wx);
-            const int gy = wrap_or_clamp(y0 + ky, p.ny, wy);
-            const int gz = wrap_or_clamp(z0 + kz, p.nz, wz);
-            // coordinates beyond a ragged box end are clamped into the box; those
-            // halo entries only feed threads that are inactive
-            const int cx = min(gx, p.nx - 1), cy = min(gy, p.ny - 1), cz = min(gz, p.nz - 1);
-            tile[kz][ky][kx] = __ldg(phi_in + cx + p.nx * (cy + p.ny * cz));
-        }
-    }
-    __syncthreads();
-    if (!active) return;
-
-    float nb[27];
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx)
-                nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
+__device__ __forceinline__ void collide_and_store(const Params &p, const Planes &pl, const Nb3 &n, const float *gv,
+                                                  const float *hv, const float *nb, float *__restrict__ phi_out,
+                                                  int *__restrict__ flag) {
     const float phic = nb[13];
     const Stencil S = stencil_sums(nb);
     float ux = 0.f, uy = 0.f, uz = 0.f;
@@ -233,6 +195,71 @@ __device__ __forceinline__ void cell_update(const Params &p, const Planes &pl, c
         dsum += (a - hv[i]) + (b - hv[i + 1]);
     }
     pop_store<15, H_SW, EDGE>(pl.h, n, 0, hv[0] - dsum);
+}
+
+
+template <int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE>
+__device__ __forceinline__ void cell_update(const Params &p, const Planes &pl, const Nb3 &n, bool active,
+                                            const float *__restrict__ phi_in, float (*tile)[HY][HX],
+                                            float *__restrict__ phi_out, int *__restrict__ flag) {
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+
+    // ---- phi^{k-1} tile with a one-cell halo (wrap on periodic axes, mirror at
+    // walls), filled row by row: warp w loads rows w, w + 8, ... of the HZ x HY
+    // rows, lane l the x-offsets l and (lanes 0, 1) 32 + l.  The loads are issued
+    // before the population loads so that their latency overlaps.
+    constexpr int NROW = HY * HZ, NWARP = TX * TY * TZ / 32, RPW = (NROW + NWARP - 1) / NWARP;
+    const int lane = tx, warp = ty + TY * tz;
+    const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
+    const int gx0 = min(wrap_or_clamp((int)blockIdx.x * TX - 1 + lane, p.nx, wx), p.nx - 1);
+    const int gx1 = min(wrap_or_clamp((int)blockIdx.x * TX + 31 + lane, p.nx, wx), p.nx - 1);
+    float tv0[RPW], tv1[RPW];
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int r = warp + k * NWARP;
+        if (r < NROW) {
+            const int kz = r / HY, ky = r - kz * HY;
+            // coordinates beyond a ragged box end are clamped into the box; those
+            // halo entries only feed threads that are inactive
+            const int gy = min(wrap_or_clamp((int)blockIdx.y * TY - 1 + ky, p.ny, wy), p.ny - 1);
+            const int gz = min(wrap_or_clamp((int)blockIdx.z * TZ - 1 + kz, p.nz, wz), p.nz - 1);
+            const float *row = phi_in + (size_t)gy * p.nx + (size_t)gz * p.nx * p.ny;
+            tv0[k] = __ldg(row + gx0);
+            if (lane < HX - 32) tv1[k] = __ldg(row + gx1);
+        }
+    }
+
+    // ---- the population loads
+    float gv[QG], hv[15];
+    if (active) {
+        if (HYDRO) {
+#pragma unroll
+            for (int i = 0; i < QG; ++i) gv[i] = pop_load<QG, G_SW, EDGE>(pl.g, n, i);
+        }
+#pragma unroll
+        for (int i = 0; i < 15; ++i) hv[i] = pop_load<15, H_SW, EDGE>(pl.h, n, i);
+    }
+
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int r = warp + k * NWARP;
+        if (r < NROW) {
+            const int kz = r / HY, ky = r - kz * HY;
+            tile[kz][ky][lane] = tv0[k];
+            if (lane < HX - 32) tile[kz][ky][32 + lane] = tv1[k];
+        }
+    }
+    __syncthreads();
+    if (!active) return;
+    float nb[27];
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx)
+                nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
+    collide_and_store<QG, G_SW, H_SW, HYDRO, EDGE>(p, pl, n, gv, hv, nb, phi_out, flag);
 }
 
 template <int QG, bool G_SW, bool H_SW, bool HYDRO>
