@@ -86,7 +86,7 @@ def kernel_source_hash() -> str:
 def recorded_traffic(workload_name: str):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
     only if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
+    path = os.path.join(ROOT, "profiles", "fused_step_kernel_roofline512_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
