@@ -83,16 +83,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_name: str):
+def recorded_traffic(workload_name: str, cells: int):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    only if it was taken on the current kernel source."""
+    only if it was taken on the current kernel source and the same box."""
     path = os.path.join(ROOT, "profiles", "fused_step_kernel_roofline512_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except Exception:
         return None
-    if rec.get("source_hash") != kernel_source_hash() or rec.get("workload") != workload_name:
+    if (rec.get("source_hash") != kernel_source_hash() or rec.get("workload") != workload_name
+            or rec.get("cells") != cells):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -207,6 +208,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world: int, cells: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank advances its own replica of `cells` cells."""
+    return world * cells * steps / seconds / 1e6
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -272,13 +290,9 @@ def main():
         torch.cuda.synchronize()
     barrier()
     sim.synchronize()
-    total_ms = t_all0.elapsed_time(t_all1)
+    total_ms = max_over_ranks(t_all0.elapsed_time(t_all1), world, "cuda")
     launch_ms = float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)]))
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * N * args.steps / (total_ms / 1e3) / 1e6
+    value = job_mlups(world, N, args.steps, total_ms / 1e3)
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -294,13 +308,9 @@ def main():
         lbm.lbm_step(sim.handle, args.steps)
         diag = lbm.lbm_reduce(sim.handle)
         lbm.lbm_get_fields(sim.handle, host_phi.data_ptr(), host_u.data_ptr(), host_p.data_ptr(), 0)
-        dt = time.perf_counter() - t0
+        dt = max_over_ranks(time.perf_counter() - t0, world, "cuda")
         barrier()
-        if world > 1:
-            tt = torch.tensor([dt], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
-        e2e = {"value": world * N * args.steps / dt / 1e6, "unit": UNIT,
+        e2e = {"value": job_mlups(world, N, args.steps, dt), "unit": UNIT,
                "h2d_bytes_per_step": N * 4 / args.steps,
                "d2h_bytes_per_step": (5 * N * 4 + 8 * lbm.LBM_DIAG_COUNT) / args.steps,
                "mass_drift": float(diag[0] / float(phi0.astype(np.float64).sum()) - 1.0)}
@@ -309,7 +319,7 @@ def main():
     algo_bytes = N * BYTES_PER_CELL[q]
     achieved = algo_bytes / (launch_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": recorded_traffic(args.workload), "peak_kind": peak_kind,
+            "traffic": recorded_traffic(args.workload, N), "peak_kind": peak_kind,
             "kernel": "fused_step_kernel<27>", "algorithmic_bytes_per_cell": BYTES_PER_CELL[q],
             "launch_ms": launch_ms}
 

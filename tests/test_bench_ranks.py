@@ -1,0 +1,72 @@
+"""Host logic of the benchmark's multi-rank (replica) mode, on CPU with gloo.
+
+Each rank advances its own replica; the job time is the slowest rank's and the
+whole-job throughput counts every rank's cells.  Two processes check the
+max-over-ranks reduction and the throughput arithmetic; the reference arm prints
+nothing on ranks other than 0.
+"""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+WORKER = r"""
+import os, sys, json
+sys.path.insert(0, {root!r})
+import torch.distributed as dist
+import bench
+rank = int(os.environ["RANK"]); world = int(os.environ["WORLD_SIZE"])
+dist.init_process_group("gloo")
+t = [0.25, 0.75][rank]
+slowest = bench.max_over_ranks(t, world, "cpu")
+print(json.dumps({{"rank": rank, "slowest": slowest,
+                  "mlups": bench.job_mlups(world, 1000, 10, slowest)}}), flush=True)
+dist.destroy_process_group()
+"""
+
+
+def test_max_over_ranks_gloo_two_processes(tmp_path):
+    import json
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "worker.py"
+    script.write_text(WORKER.format(root=root))
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port),
+                   LOCAL_RANK=str(rank))
+        procs.append(subprocess.Popen([sys.executable, str(script)], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=120)
+        assert p.returncode == 0, err
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    for o in outs:
+        assert o["slowest"] == pytest.approx(0.75)
+        assert o["mlups"] == pytest.approx(2 * 1000 * 10 / 0.75 / 1e6)
+
+
+def test_single_rank_passthrough():
+    assert bench.max_over_ranks(1.5, 1) == 1.5
+    assert bench.job_mlups(1, 134217728, 2000, 16.3) == pytest.approx(134217728 * 2000 / 16.3 / 1e6)
+
+
+def test_reference_arm_silent_off_rank_zero():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "3",
+                        "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == ""
