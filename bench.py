@@ -37,9 +37,15 @@ import workloads as W  # noqa: E402
 
 METRIC = "coupled phase-field+hydro MLUPS and % HBM roofline; FP16-store vs FP32 at stated err"
 UNIT = "MLUPS"
-# algorithmic bytes per cell update of the one-pass fused kernel (FP32):
-# read + write 15 h and q g populations, read phi once, write phi once
-BYTES_PER_CELL = {27: (15 + 27) * 4 * 2 + 4 + 4, 19: (15 + 19) * 4 * 2 + 4 + 4}
+# algorithmic bytes per cell update of the one-pass fused kernel: read + write the
+# 15 h and q g populations (rest populations FP32, moving ones in the storage
+# format), read phi once, write phi once
+STORE_BYTES = {"fp32": 4, "fp16": 2, "bf16": 2}
+
+
+def bytes_per_cell(q: int, precision: str = "fp32") -> int:
+    b = STORE_BYTES[precision]
+    return (4 + 14 * b + 4 + (q - 1) * b) * 2 + 4 + 4
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -233,6 +239,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="roofline", choices=["roofline", "rising_bubble"])
     ap.add_argument("--size", type=int, default=512, help="edge of the roofline box (512 = the benchmark)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="population storage format (arithmetic is FP32)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -267,7 +275,7 @@ def main():
     N = prob.ncells
     q = prob.q_hydro
     stream = torch.cuda.Stream()
-    sim = lbm.Simulation.from_problem(prob, stream=stream)
+    sim = lbm.Simulation.from_problem(prob, precision=args.precision, stream=stream)
     phi0_dev = torch.from_numpy(phi0).cuda()
     torch.cuda.synchronize()
     sim.init_phase(phi0_dev)
@@ -316,11 +324,11 @@ def main():
                "mass_drift": float(diag[0] / float(phi0.astype(np.float64).sum()) - 1.0)}
 
     peak, peak_kind = measured_hbm_peak()
-    algo_bytes = N * BYTES_PER_CELL[q]
+    algo_bytes = N * bytes_per_cell(q, args.precision)
     achieved = algo_bytes / (launch_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": recorded_traffic(args.workload, N), "peak_kind": peak_kind,
-            "kernel": "fused_step_kernel<27>", "algorithmic_bytes_per_cell": BYTES_PER_CELL[q],
+            "traffic": recorded_traffic(args.workload, N) if args.precision == "fp32" else None, "peak_kind": peak_kind,
+            "kernel": f"fused_step_kernel<{args.precision}, 27>", "algorithmic_bytes_per_cell": bytes_per_cell(q, args.precision),
             "launch_ms": launch_ms}
 
     if rank == 0:
@@ -329,8 +337,10 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": desc, "cells": N, "lattices": f"D3Q15+D3Q{q}", "storage": "fp32 in-place AA",
-                       "l2": f"state {N * (15 + q + 2) * 4 / 1e9:.1f} GB per GPU >> 129 MB L2, no flush needed",
+            "config": {"workload": desc, "cells": N, "lattices": f"D3Q15+D3Q{q}",
+                       "storage": f"{args.precision} populations (FP32 rest), in-place AA",
+                       "l2": f"state {N * (bytes_per_cell(q, args.precision) // 2) / 1e9:.1f} GB per GPU >> 129 MB L2, "
+                             "no flush needed",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
             "gpu_launches": args.steps,

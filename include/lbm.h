@@ -57,7 +57,13 @@ typedef enum {
     LBM_ERR_STATE = -5     /* call out of order (e.g. lbm_step before initialising) */
 } lbm_status;
 
-enum { LBM_PRECISION_FP32 = 0 };
+/* Storage of the populations in device memory.  Arithmetic is FP32 in every case.
+ * FP32: every population in FP32.  FP16 / BF16: the rest populations h_0, g_0
+ * stay FP32 and the moving ones are stored in 16 bits as shifted, scaled
+ * deviations: h_i as h_i - w_i * store_phi_ref, g_i as g_i * store_g_scale.  The
+ * rest population absorbs the rounding of the others, so the phase mass sum phi
+ * and the hydrodynamic p* are kept to FP32 rounding. */
+enum { LBM_PRECISION_FP32 = 0, LBM_PRECISION_FP16 = 1, LBM_PRECISION_BF16 = 2 };
 
 /* Box and lattices (Section 3; Section 5 uses D3Q15 for h and D3Q27 for g). */
 typedef struct {
@@ -79,10 +85,14 @@ typedef struct {
     double mobility;   /* M = tau_phi c_s^2, > 0              (eq:mobility)      */
     double gravity[3]; /* body-force acceleration g                              */
     double rho_ref;    /* buoyancy F_b = (rho - rho_ref) g; rho_ref = 0 gives F_b = rho g */
-    int precision;     /* LBM_PRECISION_FP32                                     */
+    int precision;     /* LBM_PRECISION_FP32, _FP16 or _BF16 (population storage)  */
     int clamp_phi;     /* 1: use phi clamped to [0, 1] inside rho and tau (keeps
                           rho >= rho_L when phi undershoots at high density ratio);
                           0: use phi as is                                       */
+    double store_phi_ref; /* 16-bit storage: shift of h (1 suits boxes that are mostly
+                             heavy fluid, 0 mostly light); ignored for FP32          */
+    double store_g_scale; /* 16-bit storage: power of two scaling g into the format's
+                             normal range; 0 selects 4096 (FP16) or 1 (BF16)        */
 } lbm_params;
 
 /* Diagnostics returned by lbm_reduce (FP64 accumulation).  "Light" weights a

@@ -22,7 +22,8 @@ struct lbm_t {
     char *ws;
     size_t ws_bytes;
     bool owns_ws;
-    float *h, *g, *phi[2];
+    lbm::Storage sto;
+    float *phi[2];
     int *flag;
     double *red_scratch, *red_out;
     int cur;      // phi[cur] holds phi^t
@@ -36,19 +37,26 @@ namespace {
 thread_local std::string g_create_error;
 
 struct Layout {
-    size_t h, g, phi0, phi1, flag, red_scratch, red_out, total;
+    size_t h_rest, h_mov, g_rest, g_mov, phi0, phi1, flag, red_scratch, red_out, total;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-Layout layout(const lbm_domain &d) {
-    const size_t N = (size_t)d.nx * d.ny * d.nz;
+size_t storage_bytes(int precision) { return precision == LBM_PRECISION_FP32 ? 4 : 2; }
+
+// rest plane (FP32) then the moving planes in the storage type, for h and g
+Layout layout(const lbm_domain &d, int precision) {
+    const size_t N = (size_t)d.nx * d.ny * d.nz, b = storage_bytes(precision);
     Layout L;
     size_t off = 0;
-    L.h = off;
-    off = align256(off + 15 * N * sizeof(float));
-    L.g = off;
-    off = align256(off + (size_t)d.q_hydro * N * sizeof(float));
+    L.h_rest = off;
+    off += N * sizeof(float);
+    L.h_mov = off;
+    off = align256(off + 14 * N * b);
+    L.g_rest = off;
+    off += N * sizeof(float);
+    L.g_mov = off;
+    off = align256(off + (size_t)(d.q_hydro - 1) * N * b);
     L.phi0 = off;
     off = align256(off + N * sizeof(float));
     L.phi1 = off;
@@ -84,7 +92,15 @@ lbm_status validate(const lbm_domain *d, const lbm_params *p, std::string &why) 
     if (p->sigma < 0) return why = "sigma must be >= 0", LBM_ERR_ARG;
     if (p->xi <= 0) return why = "xi must be positive", LBM_ERR_ARG;
     if (p->mobility <= 0) return why = "mobility must be positive", LBM_ERR_ARG;
-    if (p->precision != LBM_PRECISION_FP32) return why = "unsupported precision", LBM_ERR_ARG;
+    if (p->precision != LBM_PRECISION_FP32 && p->precision != LBM_PRECISION_FP16 &&
+        p->precision != LBM_PRECISION_BF16)
+        return why = "precision must be LBM_PRECISION_FP32, _FP16 or _BF16", LBM_ERR_ARG;
+    if (!finite(p->store_phi_ref) || !finite(p->store_g_scale)) return why = "storage parameters must be finite", LBM_ERR_ARG;
+    if (p->store_g_scale != 0.0) {
+        int ex = 0;
+        const double m = std::frexp(p->store_g_scale, &ex);
+        if (m != 0.5 || ex < -40 || ex > 40) return why = "store_g_scale must be 0 or a power of two", LBM_ERR_ARG;
+    }
     if (p->clamp_phi != 0 && p->clamp_phi != 1) return why = "clamp_phi must be 0 or 1", LBM_ERR_ARG;
     const double rho_L = p->rho_H / p->rho_ratio;
     const double nu_L = p->nu_H * p->rho_H / (p->mu_ratio * rho_L);
@@ -120,6 +136,15 @@ lbm::Params derive(const lbm_domain &d, const lbm_params &p) {
     k.rho_ref = (float)p.rho_ref;
     k.phi_lo = p.clamp_phi ? 0.0f : -INFINITY;
     k.phi_hi = p.clamp_phi ? 1.0f : INFINITY;
+    if (p.precision == LBM_PRECISION_FP32) {
+        k.h_ref = 0.0f;
+        k.g_scale = k.g_inv_scale = 1.0f;
+    } else {
+        const double gs = p.store_g_scale != 0.0 ? p.store_g_scale : (p.precision == LBM_PRECISION_FP16 ? 4096.0 : 1.0);
+        k.h_ref = (float)p.store_phi_ref;
+        k.g_scale = (float)gs;
+        k.g_inv_scale = (float)(1.0 / gs);
+    }
     return k;
 }
 
@@ -180,7 +205,7 @@ lbm_status lbm_workspace_size(const lbm_domain *dom, const lbm_params *prm, size
         g_create_error = why;
         return st;
     }
-    *bytes = layout(*dom).total;
+    *bytes = layout(*dom, prm->precision).total;
     return LBM_OK;
 }
 
@@ -191,7 +216,7 @@ lbm_status lbm_create(lbm_t **out, const lbm_domain *dom, const lbm_params *prm,
     std::string why;
     lbm_status st = validate(dom, prm, why);
     if (st != LBM_OK) return g_create_error = why, st;
-    const Layout L = layout(*dom);
+    const Layout L = layout(*dom, prm->precision);
     if (workspace) {
         if (workspace_bytes < L.total) return g_create_error = "workspace smaller than lbm_workspace_size()", LBM_ERR_OOM;
         if (((uintptr_t)workspace & 255) != 0) return g_create_error = "workspace must be 256-byte aligned", LBM_ERR_ARG;
@@ -223,8 +248,11 @@ lbm_status lbm_create(lbm_t **out, const lbm_domain *dom, const lbm_params *prm,
         s->owns_ws = true;
     }
     s->ws_bytes = L.total;
-    s->h = (float *)(s->ws + L.h);
-    s->g = (float *)(s->ws + L.g);
+    s->sto.precision = prm->precision;
+    s->sto.h.rest = (float *)(s->ws + L.h_rest);
+    s->sto.h.mov = s->ws + L.h_mov;
+    s->sto.g.rest = (float *)(s->ws + L.g_rest);
+    s->sto.g.mov = s->ws + L.g_mov;
     s->phi[0] = (float *)(s->ws + L.phi0);
     s->phi[1] = (float *)(s->ws + L.phi1);
     s->flag = (int *)(s->ws + L.flag);
@@ -249,10 +277,10 @@ lbm_status lbm_init_phase(lbm_t *s, const float *phi0, int phi0_on_device) {
     DeviceGuard dg(s->device);
     LBM_CK(s, cudaMemcpyAsync(s->phi[0], phi0, plane_bytes(s), kind_to_device(phi0_on_device), s->stream));
     if (!phi0_on_device) LBM_CK(s, cudaStreamSynchronize(s->stream));
-    LBM_CK(s, lbm::launch_init(s->kp, s->dom.q_hydro, s->phi[0], s->h, s->g, s->stream));
+    LBM_CK(s, lbm::launch_init(s->kp, s->sto, s->dom.q_hydro, s->phi[0], s->stream));
     LBM_CK(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
     // time level 0: the first phase-field step alone (u_{-1} = 0, phi^{-1} = phi0)
-    LBM_CK(s, lbm::launch_step(s->kp, s->dom.q_hydro, false, false, false, s->h, s->g, s->phi[0], s->phi[1], s->flag,
+    LBM_CK(s, lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, false, false, false, s->phi[0], s->phi[1], s->flag,
                                s->stream));
     s->cur = 1;
     s->t = 0;
@@ -265,8 +293,8 @@ lbm_status lbm_step(lbm_t *s, int64_t n) {
     if (!s->ready) return s->err = "lbm_step before lbm_init_phase / lbm_set_state", LBM_ERR_STATE;
     DeviceGuard dg(s->device);
     for (int64_t k = 0; k < n; ++k) {
-        LBM_CK(s, lbm::launch_step(s->kp, s->dom.q_hydro, g_swapped(s), h_swapped(s), true, s->h, s->g,
-                                   s->phi[s->cur], s->phi[s->cur ^ 1], s->flag, s->stream));
+        LBM_CK(s, lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, g_swapped(s), h_swapped(s), true, s->phi[s->cur],
+                                   s->phi[s->cur ^ 1], s->flag, s->stream));
         s->cur ^= 1;
         s->t += 1;
     }
@@ -280,7 +308,7 @@ lbm_status lbm_get_fields(lbm_t *s, float *phi, float *u, float *p, int on_devic
     const size_t N = (size_t)s->kp.N;
     const float *cur = s->phi[s->cur];
     if (on_device) {
-        LBM_CK(s, lbm::launch_fields(s->kp, s->dom.q_hydro, g_swapped(s), s->g, cur, phi, u ? u : nullptr,
+        LBM_CK(s, lbm::launch_fields(s->kp, s->sto, s->dom.q_hydro, g_swapped(s), cur, phi, u ? u : nullptr,
                                      u ? u + N : nullptr, u ? u + 2 * N : nullptr, p, s->stream));
         return LBM_OK;
     }
@@ -290,7 +318,7 @@ lbm_status lbm_get_fields(lbm_t *s, float *phi, float *u, float *p, int on_devic
     for (int comp = 0; comp < 4; ++comp) {
         float *dst = comp < 3 ? (u ? u + comp * N : nullptr) : p;
         if (!dst) continue;
-        LBM_CK(s, lbm::launch_fields(s->kp, s->dom.q_hydro, g_swapped(s), s->g, cur, nullptr,
+        LBM_CK(s, lbm::launch_fields(s->kp, s->sto, s->dom.q_hydro, g_swapped(s), cur, nullptr,
                                      comp == 0 ? stage : nullptr, comp == 1 ? stage : nullptr,
                                      comp == 2 ? stage : nullptr, comp == 3 ? stage : nullptr, s->stream));
         LBM_CK(s, cudaMemcpyAsync(dst, stage, plane_bytes(s), cudaMemcpyDeviceToHost, s->stream));
@@ -303,7 +331,7 @@ lbm_status lbm_reduce(lbm_t *s, double *out) {
     if (!s || !out) return LBM_ERR_ARG;
     if (!s->ready) return s->err = "no state yet", LBM_ERR_STATE;
     DeviceGuard dg(s->device);
-    LBM_CK(s, lbm::launch_reduce(s->kp, s->dom.q_hydro, g_swapped(s), s->g, s->phi[s->cur], s->red_scratch,
+    LBM_CK(s, lbm::launch_reduce(s->kp, s->sto, s->dom.q_hydro, g_swapped(s), s->phi[s->cur], s->red_scratch,
                                  s->red_out, s->stream));
     double raw[LBM_DIAG_COUNT];
     LBM_CK(s, cudaMemcpyAsync(raw, s->red_out, sizeof(raw), cudaMemcpyDeviceToHost, s->stream));
@@ -321,18 +349,18 @@ lbm_status lbm_get_state(lbm_t *s, float *h, float *g, float *phi, int on_device
     const size_t N = (size_t)s->kp.N;
     const int Q = s->dom.q_hydro;
     if (on_device) {
-        if (h) LBM_CK(s, lbm::launch_gather(s->kp, 15, h_swapped(s), s->h, 0, 15, h, s->stream));
-        if (g) LBM_CK(s, lbm::launch_gather(s->kp, Q, g_swapped(s), s->g, 0, Q, g, s->stream));
+        if (h) LBM_CK(s, lbm::launch_gather(s->kp, s->sto, 15, h_swapped(s), 0, 15, h, s->stream));
+        if (g) LBM_CK(s, lbm::launch_gather(s->kp, s->sto, Q, g_swapped(s), 0, Q, g, s->stream));
         if (phi) LBM_CK(s, cudaMemcpyAsync(phi, s->phi[s->cur], plane_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
         return LBM_OK;
     }
     float *stage = s->phi[s->cur ^ 1];
     for (int i = 0; h && i < 15; ++i) {
-        LBM_CK(s, lbm::launch_gather(s->kp, 15, h_swapped(s), s->h, i, i + 1, stage, s->stream));
+        LBM_CK(s, lbm::launch_gather(s->kp, s->sto, 15, h_swapped(s), i, i + 1, stage, s->stream));
         LBM_CK(s, cudaMemcpyAsync(h + i * N, stage, plane_bytes(s), cudaMemcpyDeviceToHost, s->stream));
     }
     for (int i = 0; g && i < Q; ++i) {
-        LBM_CK(s, lbm::launch_gather(s->kp, Q, g_swapped(s), s->g, i, i + 1, stage, s->stream));
+        LBM_CK(s, lbm::launch_gather(s->kp, s->sto, Q, g_swapped(s), i, i + 1, stage, s->stream));
         LBM_CK(s, cudaMemcpyAsync(g + i * N, stage, plane_bytes(s), cudaMemcpyDeviceToHost, s->stream));
     }
     if (phi) LBM_CK(s, cudaMemcpyAsync(phi, s->phi[s->cur], plane_bytes(s), cudaMemcpyDeviceToHost, s->stream));
@@ -348,18 +376,18 @@ lbm_status lbm_set_state(lbm_t *s, const float *h, const float *g, const float *
     // the state becomes time level 0: g natural, h one AA step ahead (swapped)
     s->t = 0;
     if (on_device) {
-        LBM_CK(s, lbm::launch_scatter(s->kp, 15, h_swapped(s), s->h, 0, 15, h, s->stream));
-        LBM_CK(s, lbm::launch_scatter(s->kp, Q, g_swapped(s), s->g, 0, Q, g, s->stream));
+        LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, 15, h_swapped(s), 0, 15, h, s->stream));
+        LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, Q, g_swapped(s), 0, Q, g, s->stream));
         LBM_CK(s, cudaMemcpyAsync(s->phi[s->cur], phi, plane_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
     } else {
         float *stage = s->phi[s->cur ^ 1];
         for (int i = 0; i < 15; ++i) {
             LBM_CK(s, cudaMemcpyAsync(stage, h + i * N, plane_bytes(s), cudaMemcpyHostToDevice, s->stream));
-            LBM_CK(s, lbm::launch_scatter(s->kp, 15, h_swapped(s), s->h, i, i + 1, stage, s->stream));
+            LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, 15, h_swapped(s), i, i + 1, stage, s->stream));
         }
         for (int i = 0; i < Q; ++i) {
             LBM_CK(s, cudaMemcpyAsync(stage, g + i * N, plane_bytes(s), cudaMemcpyHostToDevice, s->stream));
-            LBM_CK(s, lbm::launch_scatter(s->kp, Q, g_swapped(s), s->g, i, i + 1, stage, s->stream));
+            LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, Q, g_swapped(s), i, i + 1, stage, s->stream));
         }
         LBM_CK(s, cudaMemcpyAsync(s->phi[s->cur], phi, plane_bytes(s), cudaMemcpyHostToDevice, s->stream));
         LBM_CK(s, cudaStreamSynchronize(s->stream));

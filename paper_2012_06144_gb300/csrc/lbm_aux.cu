@@ -1,22 +1,38 @@
 // lbm_aux.cu -- initialisation, field extraction, state transfer and FP64
-// diagnostics for the conservative Allen-Cahn LBM.
+// diagnostics for the conservative Allen-Cahn LBM, for every population storage
+// type (FP32, FP16, BF16 moving populations; FP32 rest populations).
 #include "lbm_internal.h"
 
 namespace lbm {
 
-// ---------------------------------------------------------------------------
-// h_i = w_i phi0 (= phi0 Gamma_i at u = 0, Section 3.1), g_i = 0 (p* = 0, u = 0).
-template <int QG>
-__global__ void init_kernel(long long N, const float *__restrict__ phi0, float *__restrict__ h,
-                            float *__restrict__ g) {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const float f = phi0[c];
-#pragma unroll
-        for (int i = 0; i < 15; ++i) h[i * N + c] = wgt<15>(i) * f;
-#pragma unroll
-        for (int i = 0; i < QG; ++i) g[i * N + c] = 0.f;
-    }
+template <typename T>
+static LatView<T> h_view(const Params &p, const Storage &s) {
+    return {s.h.rest, static_cast<T *>(s.h.mov), p.N, p.h_ref, 1.0f, 1.0f};
 }
+
+template <typename T>
+static LatView<T> g_view(const Params &p, const Storage &s) {
+    return {s.g.rest, static_cast<T *>(s.g.mov), p.N, 0.0f, p.g_scale, p.g_inv_scale};
+}
+
+// Runs F<T> for the storage type of s.
+#define LBM_BY_PRECISION(s, ...)                       \
+    switch ((s).precision) {                           \
+        case LBM_PRECISION_FP32: {                     \
+            using T = float;                           \
+            __VA_ARGS__;                               \
+        } break;                                       \
+        case LBM_PRECISION_FP16: {                     \
+            using T = __half;                          \
+            __VA_ARGS__;                               \
+        } break;                                       \
+        case LBM_PRECISION_BF16: {                     \
+            using T = __nv_bfloat16;                   \
+            __VA_ARGS__;                               \
+        } break;                                       \
+        default:                                       \
+            return cudaErrorInvalidValue;              \
+    }
 
 static dim3 grid1d(long long N) {
     long long b = (N + 255) / 256;
@@ -24,24 +40,51 @@ static dim3 grid1d(long long N) {
     return dim3((unsigned)(b > 0 ? b : 1));
 }
 
-cudaError_t launch_init(const Params &p, int q, const float *phi0, float *h, float *g, cudaStream_t st) {
-    if (q == 19)
-        init_kernel<19><<<grid1d(p.N), 256, 0, st>>>(p.N, phi0, h, g);
-    else if (q == 27)
-        init_kernel<27><<<grid1d(p.N), 256, 0, st>>>(p.N, phi0, h, g);
-    else
-        return cudaErrorInvalidValue;
+static dim3 grid3d(const Params &p) { return dim3((p.nx + 31) / 32, (p.ny + 7) / 8, p.nz); }
+
+// ---------------------------------------------------------------------------
+// h_i = w_i phi0 (= phi0 Gamma_i at u = 0, Section 3.1), g_i = 0 (p* = 0, u = 0).
+template <typename T, int QG>
+__global__ void init_kernel(long long N, const float *__restrict__ phi0, LatView<T> h, LatView<T> g) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const float f = phi0[c];
+#pragma unroll
+        for (int i = 0; i < 15; ++i) h.template store<15>(i, i, c, wgt<15>(i) * f);
+#pragma unroll
+        for (int i = 0; i < QG; ++i) g.template store<QG>(i, i, c, 0.f);
+    }
+}
+
+cudaError_t launch_init(const Params &p, const Storage &sto, int q, const float *phi0, cudaStream_t st) {
+    LBM_BY_PRECISION(sto, {
+        if (q == 19)
+            init_kernel<T, 19><<<grid1d(p.N), 256, 0, st>>>(p.N, phi0, h_view<T>(p, sto), g_view<T>(p, sto));
+        else if (q == 27)
+            init_kernel<T, 27><<<grid1d(p.N), 256, 0, st>>>(p.N, phi0, h_view<T>(p, sto), g_view<T>(p, sto));
+        else
+            return cudaErrorInvalidValue;
+    })
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Macroscopic fields at time level t from (g^t, phi^t): the hydro-step formulas
 // of Section 3.2 evaluated without collision.
-template <int QG, bool G_SW>
-__global__ void __launch_bounds__(256) fields_kernel(Params p, const float *__restrict__ g,
-                                                     const float *__restrict__ phi, float *__restrict__ out_phi,
-                                                     float *__restrict__ ux, float *__restrict__ uy,
-                                                     float *__restrict__ uz, float *__restrict__ pr) {
+template <typename T, int QG, bool G_SW>
+__device__ __forceinline__ void load_g(const Params &p, const LatView<T> &g, const Cell &C, float gv[QG]) {
+#pragma unroll
+    for (int i = 0; i < QG; ++i) {
+        int slot, idx;
+        pop_src_loc<QG, G_SW>(C, i, slot, idx);
+        gv[i] = g.template load<QG>(slot, i, idx);
+    }
+}
+
+template <typename T, int QG, bool G_SW>
+__global__ void __launch_bounds__(256) fields_kernel(Params p, LatView<T> g, const float *__restrict__ phi,
+                                                     float *__restrict__ out_phi, float *__restrict__ ux,
+                                                     float *__restrict__ uy, float *__restrict__ uz,
+                                                     float *__restrict__ pr) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -50,8 +93,7 @@ __global__ void __launch_bounds__(256) fields_kernel(Params p, const float *__re
     float nb[27];
     gather_phi(phi, C, nb);
     float gv[QG];
-#pragma unroll
-    for (int i = 0; i < QG; ++i) gv[i] = g[pop_src<QG, G_SW>(C, p.N, i)];
+    load_g<T, QG, G_SW>(p, g, C, gv);
     Hydro<QG> H;
     hydro_macro<QG>(p, gv, nb[13], stencil_sums(nb), H);
     if (out_phi) out_phi[C.c] = nb[13];
@@ -61,80 +103,96 @@ __global__ void __launch_bounds__(256) fields_kernel(Params p, const float *__re
     if (pr) pr[C.c] = H.pstar * H.rho * (1.0f / 3.0f);  // p = p* rho c_s^2
 }
 
-static dim3 grid3d(const Params &p) { return dim3((p.nx + 31) / 32, (p.ny + 7) / 8, p.nz); }
-
-cudaError_t launch_fields(const Params &p, int q, bool gsw, const float *g, const float *phi, float *out_phi,
+cudaError_t launch_fields(const Params &p, const Storage &sto, int q, bool gsw, const float *phi, float *out_phi,
                           float *ux, float *uy, float *uz, float *pr, cudaStream_t st) {
     const dim3 b(32, 8, 1), gr = grid3d(p);
-    if (q == 19 && gsw)
-        fields_kernel<19, true><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
-    else if (q == 19)
-        fields_kernel<19, false><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
-    else if (q == 27 && gsw)
-        fields_kernel<27, true><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
-    else if (q == 27)
-        fields_kernel<27, false><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
-    else
-        return cudaErrorInvalidValue;
+    LBM_BY_PRECISION(sto, {
+        const LatView<T> g = g_view<T>(p, sto);
+        if (q == 19 && gsw)
+            fields_kernel<T, 19, true><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
+        else if (q == 19)
+            fields_kernel<T, 19, false><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
+        else if (q == 27 && gsw)
+            fields_kernel<T, 27, true><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
+        else if (q == 27)
+            fields_kernel<T, 27, false><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
+        else
+            return cudaErrorInvalidValue;
+    })
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// State transfer between the in-place AA storage and dense natural planes.
-template <int Q, bool SW>
-__global__ void gather_kernel(Params p, const float *__restrict__ A, int i0, int i1, float *__restrict__ out) {
+// State transfer between the in-place AA storage and dense natural FP32 planes.
+template <typename T, int Q, bool SW>
+__global__ void gather_kernel(Params p, LatView<T> A, int i0, int i1, float *__restrict__ out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
     const Cell C = make_cell(p, x, y, z);
-    for (int i = i0; i < i1; ++i) out[(size_t)(i - i0) * p.N + C.c] = A[pop_src<Q, SW>(C, p.N, i)];
+    for (int i = i0; i < i1; ++i) {
+        int slot, idx;
+        pop_src_loc<Q, SW>(C, i, slot, idx);
+        out[(size_t)(i - i0) * p.N + C.c] = A.template load<Q>(slot, i, idx);
+    }
 }
 
-template <int Q, bool SW>
-__global__ void scatter_kernel(Params p, float *__restrict__ A, int i0, int i1, const float *__restrict__ in) {
+template <typename T, int Q, bool SW>
+__global__ void scatter_kernel(Params p, LatView<T> A, int i0, int i1, const float *__restrict__ in) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= p.nx || y >= p.ny) return;
     const Cell C = make_cell(p, x, y, z);
-    for (int i = i0; i < i1; ++i) A[pop_src<Q, SW>(C, p.N, i)] = in[(size_t)(i - i0) * p.N + C.c];
+    for (int i = i0; i < i1; ++i) {
+        int slot, idx;
+        pop_src_loc<Q, SW>(C, i, slot, idx);
+        A.template store<Q>(slot, i, idx, in[(size_t)(i - i0) * p.N + C.c]);
+    }
 }
 
-template <bool GATHER, int Q>
-static cudaError_t transfer_q(const Params &p, bool sw, float *A, int i0, int i1, float *buf, cudaStream_t st) {
+template <typename T, int Q>
+static void transfer_q(const Params &p, const LatView<T> &A, bool gather, bool sw, int i0, int i1, float *buf,
+                       cudaStream_t st) {
     const dim3 b(32, 8, 1), gr = grid3d(p);
-    if (GATHER) {
+    if (gather) {
         if (sw)
-            gather_kernel<Q, true><<<gr, b, 0, st>>>(p, A, i0, i1, buf);
+            gather_kernel<T, Q, true><<<gr, b, 0, st>>>(p, A, i0, i1, buf);
         else
-            gather_kernel<Q, false><<<gr, b, 0, st>>>(p, A, i0, i1, buf);
+            gather_kernel<T, Q, false><<<gr, b, 0, st>>>(p, A, i0, i1, buf);
     } else {
         if (sw)
-            scatter_kernel<Q, true><<<gr, b, 0, st>>>(p, A, i0, i1, buf);
+            scatter_kernel<T, Q, true><<<gr, b, 0, st>>>(p, A, i0, i1, buf);
         else
-            scatter_kernel<Q, false><<<gr, b, 0, st>>>(p, A, i0, i1, buf);
+            scatter_kernel<T, Q, false><<<gr, b, 0, st>>>(p, A, i0, i1, buf);
     }
+}
+
+static cudaError_t transfer(const Params &p, const Storage &sto, int q, bool gather, bool sw, int i0, int i1,
+                            float *buf, cudaStream_t st) {
+    if (i0 < 0 || i1 > q || i0 >= i1) return cudaErrorInvalidValue;
+    LBM_BY_PRECISION(sto, {
+        if (q == 15)
+            transfer_q<T, 15>(p, h_view<T>(p, sto), gather, sw, i0, i1, buf, st);
+        else if (q == 19)
+            transfer_q<T, 19>(p, g_view<T>(p, sto), gather, sw, i0, i1, buf, st);
+        else if (q == 27)
+            transfer_q<T, 27>(p, g_view<T>(p, sto), gather, sw, i0, i1, buf, st);
+        else
+            return cudaErrorInvalidValue;
+    })
     return cudaGetLastError();
 }
 
-template <bool GATHER>
-static cudaError_t transfer(const Params &p, int q, bool sw, float *A, int i0, int i1, float *buf, cudaStream_t st) {
-    if (i0 < 0 || i1 > q || i0 >= i1) return cudaErrorInvalidValue;
-    if (q == 15) return transfer_q<GATHER, 15>(p, sw, A, i0, i1, buf, st);
-    if (q == 19) return transfer_q<GATHER, 19>(p, sw, A, i0, i1, buf, st);
-    if (q == 27) return transfer_q<GATHER, 27>(p, sw, A, i0, i1, buf, st);
-    return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_gather(const Params &p, int q, bool sw, const float *A, int i0, int i1, float *out,
+cudaError_t launch_gather(const Params &p, const Storage &sto, int q, bool sw, int i0, int i1, float *out,
                           cudaStream_t st) {
-    return transfer<true>(p, q, sw, const_cast<float *>(A), i0, i1, out, st);
+    return transfer(p, sto, q, true, sw, i0, i1, out, st);
 }
 
-cudaError_t launch_scatter(const Params &p, int q, bool sw, float *A, int i0, int i1, const float *in,
+cudaError_t launch_scatter(const Params &p, const Storage &sto, int q, bool sw, int i0, int i1, const float *in,
                            cudaStream_t st) {
-    return transfer<false>(p, q, sw, A, i0, i1, const_cast<float *>(in), st);
+    return transfer(p, sto, q, false, sw, i0, i1, const_cast<float *>(in), st);
 }
 
 // ---------------------------------------------------------------------------
@@ -154,9 +212,8 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-template <int QG, bool G_SW>
-__global__ void __launch_bounds__(256) reduce_partial_kernel(Params p, const float *__restrict__ g,
-                                                             const float *__restrict__ phi,
+template <typename T, int QG, bool G_SW>
+__global__ void __launch_bounds__(256) reduce_partial_kernel(Params p, LatView<T> g, const float *__restrict__ phi,
                                                              double *__restrict__ scratch) {
     double acc[kDiagSlots];
 #pragma unroll
@@ -171,8 +228,7 @@ __global__ void __launch_bounds__(256) reduce_partial_kernel(Params p, const flo
         float nb[27];
         gather_phi(phi, C, nb);
         float gv[QG];
-#pragma unroll
-        for (int i = 0; i < QG; ++i) gv[i] = g[pop_src<QG, G_SW>(C, p.N, i)];
+        load_g<T, QG, G_SW>(p, g, C, gv);
         Hydro<QG> H;
         hydro_macro<QG>(p, gv, nb[13], stencil_sums(nb), H);
         const double f = nb[13], lf = 1.0 - f, rho = H.rho;
@@ -228,18 +284,21 @@ __global__ void __launch_bounds__(256) reduce_final_kernel(const double *__restr
     }
 }
 
-cudaError_t launch_reduce(const Params &p, int q, bool gsw, const float *g, const float *phi, double *scratch,
+cudaError_t launch_reduce(const Params &p, const Storage &sto, int q, bool gsw, const float *phi, double *scratch,
                           double *out, cudaStream_t st) {
-    if (q == 19 && gsw)
-        reduce_partial_kernel<19, true><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);
-    else if (q == 19)
-        reduce_partial_kernel<19, false><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);
-    else if (q == 27 && gsw)
-        reduce_partial_kernel<27, true><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);
-    else if (q == 27)
-        reduce_partial_kernel<27, false><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);
-    else
-        return cudaErrorInvalidValue;
+    LBM_BY_PRECISION(sto, {
+        const LatView<T> g = g_view<T>(p, sto);
+        if (q == 19 && gsw)
+            reduce_partial_kernel<T, 19, true><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);
+        else if (q == 19)
+            reduce_partial_kernel<T, 19, false><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);
+        else if (q == 27 && gsw)
+            reduce_partial_kernel<T, 27, true><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);
+        else if (q == 27)
+            reduce_partial_kernel<T, 27, false><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);
+        else
+            return cudaErrorInvalidValue;
+    })
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     reduce_final_kernel<<<1, 256, 0, st>>>(scratch, kReduceBlocks, out);

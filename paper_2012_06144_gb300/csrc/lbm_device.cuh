@@ -14,8 +14,12 @@
 // to (opp(i), x)) instead.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <cstddef>
 #include <cstdint>
+#include <type_traits>
 
 namespace lbm {
 
@@ -75,6 +79,26 @@ __host__ __device__ constexpr float wgt(int i) {
     return e2 == 0 ? 8.0f / 27.0f : (e2 == 1 ? 2.0f / 27.0f : (e2 == 2 ? 1.0f / 54.0f : 1.0f / 216.0f));
 }
 
+// ---------------------------------------------------------------------------
+// Population storage.  Every lattice is one rest plane in FP32 followed by q-1
+// planes of its moving populations in a storage type T: float, __half or
+// __nv_bfloat16.  A moving population f_i is kept as (f_i - w_i ref) * scale
+// with a per-field shift ref and a power-of-two scale; the stored value decodes
+// back exactly as w_i ref + q / scale.  With T = float, ref = 0 and scale = 1.
+template <typename T>
+__device__ __forceinline__ float to_f(T v) {
+    if constexpr (std::is_same<T, __half>::value) return __half2float(v);
+    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __bfloat162float(v);
+    else return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T from_f(float v) {
+    if constexpr (std::is_same<T, __half>::value) return __float2half_rn(v);
+    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __float2bfloat16_rn(v);
+    else return v;
+}
+
 // Kernel-side copy of the problem (derived in lbm_create).
 struct Params {
     int nx, ny, nz;
@@ -88,6 +112,34 @@ struct Params {
     float inv_xi;
     float gx, gy, gz, rho_ref;
     float phi_lo, phi_hi;  // phi is clamped to [phi_lo, phi_hi] inside rho and tau
+    // reduced-precision storage of the moving populations (ignored for FP32):
+    // h_i stored as h_i - w_i h_ref, g_i stored as g_i * g_scale
+    float h_ref, g_scale, g_inv_scale;
+};
+
+// One lattice as seen by the auxiliary kernels: slot 0 (rest) in FP32, slot s >= 1
+// at mov[(s - 1) N] in type T.
+template <typename T>
+struct LatView {
+    float *rest;
+    T *mov;
+    long long N;
+    float ref, scale, inv_scale;
+
+    template <int Q>
+    __device__ __forceinline__ float load(size_t slot, int dir, size_t idx) const {
+        if (slot == 0) return rest[idx];
+        const T q = mov[(slot - 1) * N + idx];
+        if constexpr (std::is_same<T, float>::value) return q;
+        else return fmaf(to_f(q), inv_scale, wgt<Q>(dir) * ref);
+    }
+    // stores v (already a value that encodes exactly, or any value for slot 0)
+    template <int Q>
+    __device__ __forceinline__ void store(size_t slot, int dir, size_t idx, float v) const {
+        if (slot == 0) rest[idx] = v;
+        else if constexpr (std::is_same<T, float>::value) mov[(slot - 1) * N + idx] = v;
+        else mov[(slot - 1) * N + idx] = from_f<T>((v - wgt<Q>(dir) * ref) * scale);
+    }
 };
 
 // Per-thread geometry: neighbour offsets along each axis (periodic wrap, or
@@ -142,6 +194,24 @@ __device__ __forceinline__ size_t pop_src(const Cell &C, long long N, int i) {
     const V3 e = vel<Q>(i);
     if (leaves(C, e, -1)) return (size_t)i * N + C.c;
     return (size_t)opp(i) * N + nbr(C, -e.x, -e.y, -e.z);
+}
+
+// The same location as (slot, element).
+template <int Q, bool SWAPPED>
+__device__ __forceinline__ void pop_src_loc(const Cell &C, int i, int &slot, int &idx) {
+    if (!SWAPPED) {
+        slot = i;
+        idx = C.c;
+        return;
+    }
+    const V3 e = vel<Q>(i);
+    if (leaves(C, e, -1)) {
+        slot = i;
+        idx = C.c;
+        return;
+    }
+    slot = opp(i);
+    idx = nbr(C, -e.x, -e.y, -e.z);
 }
 
 // Location that receives the post-collision f*_i(x).

@@ -10,30 +10,43 @@
 
 namespace lbm {
 
+// Device memory of one lattice: the FP32 rest plane and q-1 planes of moving
+// populations in the storage type selected by Storage::precision.
+struct LatticeMem {
+    float *rest;
+    void *mov;
+};
+
+struct Storage {
+    int precision;  // LBM_PRECISION_*
+    LatticeMem h, g;
+};
+
 // One launch of the fused kernel K_k = hydro(k-1) + phase(k) (hydro = true), or
 // the first phase step alone (hydro = false).  g_swapped / h_swapped give the
 // current AA layout of each lattice.
-cudaError_t launch_step(const Params &p, int q_hydro, bool g_swapped, bool h_swapped, bool hydro, float *h,
-                        float *g, const float *phi_in, float *phi_out, int *flag, cudaStream_t st);
+cudaError_t launch_step(const Params &p, const Storage &sto, int q_hydro, bool g_swapped, bool h_swapped,
+                        bool hydro, const float *phi_in, float *phi_out, int *flag, cudaStream_t st);
 
 // h_i = w_i phi0, g_i = 0 (natural layout).
-cudaError_t launch_init(const Params &p, int q_hydro, const float *phi0, float *h, float *g, cudaStream_t st);
+cudaError_t launch_init(const Params &p, const Storage &sto, int q_hydro, const float *phi0, cudaStream_t st);
 
 // phi, u (three planes), p from (g^t, phi^t); outputs may be null.
-cudaError_t launch_fields(const Params &p, int q_hydro, bool g_swapped, const float *g, const float *phi,
+cudaError_t launch_fields(const Params &p, const Storage &sto, int q_hydro, bool g_swapped, const float *phi,
                           float *out_phi, float *ux, float *uy, float *uz, float *pr, cudaStream_t st);
 
-// Natural-layout planes [i0, i1) of a lattice to/from a dense buffer.
-cudaError_t launch_gather(const Params &p, int q, bool swapped, const float *A, int i0, int i1, float *out,
+// Natural-layout planes [i0, i1) of one lattice (q = 15: h, else g) to/from a
+// dense FP32 buffer.
+cudaError_t launch_gather(const Params &p, const Storage &sto, int q, bool swapped, int i0, int i1, float *out,
                           cudaStream_t st);
-cudaError_t launch_scatter(const Params &p, int q, bool swapped, float *A, int i0, int i1, const float *in,
-                           cudaStream_t st);
+cudaError_t launch_scatter(const Params &p, const Storage &sto, int q, bool swapped, int i0, int i1,
+                           const float *in, cudaStream_t st);
 
 // Diagnostics: LBM_DIAG_COUNT raw sums / max into out (device); scratch holds
 // kReduceBlocks * kDiagSlots doubles.
 constexpr int kReduceBlocks = 1024;
 constexpr int kDiagSlots = 12;
-cudaError_t launch_reduce(const Params &p, int q_hydro, bool g_swapped, const float *g, const float *phi,
+cudaError_t launch_reduce(const Params &p, const Storage &sto, int q_hydro, bool g_swapped, const float *phi,
                           double *scratch, double *out, cudaStream_t st);
 
 // Validates a problem and derives the kernel parameters (defined with the C ABI).

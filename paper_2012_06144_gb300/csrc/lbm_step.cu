@@ -44,9 +44,11 @@ namespace lbm {
 constexpr int TX = 32, TY = LBM_TY, TZ = LBM_TZ;
 constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 
+// Plane pointers of both lattices: slot 0 (rest) is FP32, slots >= 1 hold the
+// moving populations in the storage type of the launch.
 struct Planes {
-    float *h[15];
-    float *g[27];
+    void *h[15];
+    void *g[27];
 };
 
 // Per-thread neighbour offsets: element index of (x+dx, y+dy, z+dz) is
@@ -66,7 +68,8 @@ __device__ __forceinline__ bool leaves3(const Nb3 &n, V3 e, int sign) {
            (ez > 0 && (n.hi & 4)) || (ez < 0 && (n.lo & 4));
 }
 
-__device__ __forceinline__ float ld_pop(const float *a) {
+template <typename T>
+__device__ __forceinline__ T ld_pop(const T *a) {
 #if LBM_STREAM_HINTS
     return __ldcs(a);
 #else
@@ -74,7 +77,8 @@ __device__ __forceinline__ float ld_pop(const float *a) {
 #endif
 }
 
-__device__ __forceinline__ void st_pop(float *a, float v) {
+template <typename T>
+__device__ __forceinline__ void st_pop(T *a, T v) {
 #if LBM_STREAM_HINTS
     __stcs(a, v);
 #else
@@ -82,36 +86,90 @@ __device__ __forceinline__ void st_pop(float *a, float v) {
 #endif
 }
 
-// pre-collision f_i(x) of a lattice in the AA layout (see lbm_device.cuh)
+// Storage of the moving populations of one lattice in type T: the stored value q
+// decodes as w_i ref + q inv_scale and encodes as (f - w_i ref) scale.
+template <typename T>
+struct Codec {
+    float ref, scale, inv_scale;
+    template <int Q>
+    __device__ __forceinline__ float decode(T q, int i) const {
+        if constexpr (std::is_same<T, float>::value) return q;
+        else return fmaf(to_f(q), inv_scale, wgt<Q>(i) * ref);
+    }
+    template <int Q>
+    __device__ __forceinline__ T encode(float f, int i) const {
+        if constexpr (std::is_same<T, float>::value) return f;
+        else return from_f<T>((f - wgt<Q>(i) * ref) * scale);
+    }
+};
+
+// (slot, element) holding the pre-collision f_i(x) in the AA layout (see lbm_device.cuh)
 template <int Q, bool SW, bool EDGE>
-__device__ __forceinline__ float pop_load(float *const *pl, const Nb3 &n, int i) {
-    if (!SW) return ld_pop(pl[i] + n.X[1]);
+__device__ __forceinline__ void src_loc(const Nb3 &n, int i, int &slot, int &idx) {
+    if (!SW) {
+        slot = i;
+        idx = n.X[1];
+        return;
+    }
     const V3 e = vel<Q>(i);
-    if (EDGE && leaves3(n, e, -1)) return ld_pop(pl[i] + n.X[1]);
-    return ld_pop(pl[opp(i)] + nidx(n, -e.x, -e.y, -e.z));
+    if (EDGE && leaves3(n, e, -1)) {
+        slot = i;
+        idx = n.X[1];
+        return;
+    }
+    slot = opp(i);
+    idx = nidx(n, -e.x, -e.y, -e.z);
 }
 
+// (slot, element) that receives the post-collision f*_i(x)
 template <int Q, bool SW, bool EDGE>
-__device__ __forceinline__ void pop_store(float *const *pl, const Nb3 &n, int i, float v) {
+__device__ __forceinline__ void dst_loc(const Nb3 &n, int i, int &slot, int &idx) {
     if (!SW) {
-        st_pop(pl[opp(i)] + n.X[1], v);
+        slot = opp(i);
+        idx = n.X[1];
         return;
     }
     const V3 e = vel<Q>(i);
     if (EDGE && leaves3(n, e, +1)) {
-        st_pop(pl[opp(i)] + n.X[1], v);
+        slot = opp(i);
+        idx = n.X[1];
         return;
     }
-    st_pop(pl[i] + nidx(n, e.x, e.y, e.z), v);
+    slot = i;
+    idx = nidx(n, e.x, e.y, e.z);
+}
+
+template <typename T, int Q, bool SW, bool EDGE>
+__device__ __forceinline__ float pop_load(void *const *pl, const Nb3 &n, int i, const Codec<T> &cd) {
+    int slot, idx;
+    src_loc<Q, SW, EDGE>(n, i, slot, idx);
+    if (slot == 0) return ld_pop(static_cast<const float *>(pl[0]) + idx);
+    return cd.template decode<Q>(ld_pop(static_cast<const T *>(pl[slot]) + idx), i);
+}
+
+// stores the rest population (i = 0, FP32) or an encoded moving population
+template <typename T, int Q, bool SW, bool EDGE>
+__device__ __forceinline__ void pop_store_rest(void *const *pl, const Nb3 &n, float v) {
+    int slot, idx;
+    dst_loc<Q, SW, EDGE>(n, 0, slot, idx);
+    st_pop(static_cast<float *>(pl[0]) + idx, v);
+}
+
+template <typename T, int Q, bool SW, bool EDGE>
+__device__ __forceinline__ void pop_store_enc(void *const *pl, const Nb3 &n, int i, T q) {
+    int slot, idx;
+    dst_loc<Q, SW, EDGE>(n, i, slot, idx);
+    st_pop(static_cast<T *>(pl[slot]) + idx, q);
 }
 
 // Collision of both lattices at one cell and the streaming stores, from the
 // pre-collision populations gv (g^{k-1}), hv (h^k) and the 3x3x3 neighbourhood nb
 // of phi^{k-1}.
-template <int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE>
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE>
 __device__ __forceinline__ void collide_and_store(const Params &p, const Planes &pl, const Nb3 &n, const float *gv,
                                                   const float *hv, const float *nb, float *__restrict__ phi_out,
                                                   int *__restrict__ flag) {
+    const Codec<T> ch{p.h_ref, 1.0f, 1.0f}, cg{0.0f, p.g_scale, p.g_inv_scale};
     const float phic = nb[13];
     const Stencil S = stencil_sums(nb);
     float ux = 0.f, uy = 0.f, uz = 0.f;
@@ -121,19 +179,20 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const Planes 
         Hydro<QG> Hd;
         hydro_macro<QG>(p, gv, phic, S, Hd);
         const HydroPost<QG> P = hydro_post<QG>(Hd);
-        // the rest population takes the remainder of the zeroth moment, so that
-        // sum_i g*_i = p* holds to rounding (the FP32 weights do not sum to 1)
+        // The rest population takes p* - sum_{i>0} g*_i, with each g*_i as the next
+        // reader will decode it, so the stored populations keep the zeroth moment
+        // p* of eq:improved_collision to rounding (the FP32 weights do not sum to 1).
         float gsum = 0.f;
 #pragma unroll
         for (int i = 1; i < QG; i += 2) {
             float E, O;
             hydro_gstar_pair<QG>(P, i, E, O);
-            const float a = E + O, b = E - O;
-            pop_store<QG, G_SW, EDGE>(pl.g, n, i, a);
-            pop_store<QG, G_SW, EDGE>(pl.g, n, i + 1, b);
-            gsum += a + b;
+            const T qa = cg.template encode<QG>(E + O, i), qb = cg.template encode<QG>(E - O, i + 1);
+            pop_store_enc<T, QG, G_SW, EDGE>(pl.g, n, i, qa);
+            pop_store_enc<T, QG, G_SW, EDGE>(pl.g, n, i + 1, qb);
+            gsum += cg.template decode<QG>(qa, i) + cg.template decode<QG>(qb, i + 1);
         }
-        pop_store<QG, G_SW, EDGE>(pl.g, n, 0, Hd.pstar - gsum);
+        pop_store_rest<T, QG, G_SW, EDGE>(pl.g, n, Hd.pstar - gsum);
         ux = Hd.ux;
         uy = Hd.uy;
         uz = Hd.uz;
@@ -171,10 +230,10 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const Planes 
     // h^eq = phi_k w (1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u) and F_i = theta w e.n.
     // The non-equilibrium h^eq_i - h_i is formed as fma(phi_k, w, -h_i) + phi_k w
     // (velocity terms), so it carries no rounding of the large product phi w.
-    // The rest population takes h_0 - sum_{i>0} (h*_i - h_i): each increment is
-    // exact in FP32 (h*_i and h_i are close), so the stored populations sum to
-    // the incoming sum_i h_i up to the rounding of small increments, i.e. the
-    // cell's phase mass is kept.
+    // The rest population takes h_0 - sum_{i>0} (h*_i - h_i), with each h*_i as
+    // the next reader will decode it: each increment is exact in FP32 (h*_i and
+    // h_i are close), so the stored populations sum to the incoming sum_i h_i up
+    // to the rounding of small increments, i.e. the cell's phase mass is kept.
     float dsum = 0.f;
 #pragma unroll
     for (int i = 1; i < 15; i += 2) {
@@ -190,15 +249,15 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const Planes 
         const float neq_b = fmaf(phik, w, -hv[i + 1]) + (x_even - x_odd);
         const float a = hv[i] + fmaf(om, neq_a, F);
         const float b = hv[i + 1] + fmaf(om, neq_b, -F);
-        pop_store<15, H_SW, EDGE>(pl.h, n, i, a);
-        pop_store<15, H_SW, EDGE>(pl.h, n, i + 1, b);
-        dsum += (a - hv[i]) + (b - hv[i + 1]);
+        const T qa = ch.template encode<15>(a, i), qb = ch.template encode<15>(b, i + 1);
+        pop_store_enc<T, 15, H_SW, EDGE>(pl.h, n, i, qa);
+        pop_store_enc<T, 15, H_SW, EDGE>(pl.h, n, i + 1, qb);
+        dsum += (ch.template decode<15>(qa, i) - hv[i]) + (ch.template decode<15>(qb, i + 1) - hv[i + 1]);
     }
-    pop_store<15, H_SW, EDGE>(pl.h, n, 0, hv[0] - dsum);
+    pop_store_rest<T, 15, H_SW, EDGE>(pl.h, n, hv[0] - dsum);
 }
 
-
-template <int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE>
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE>
 __device__ __forceinline__ void cell_update(const Params &p, const Planes &pl, const Nb3 &n, bool active,
                                             const float *__restrict__ phi_in, float (*tile)[HY][HX],
                                             float *__restrict__ phi_out, int *__restrict__ flag) {
@@ -230,14 +289,15 @@ __device__ __forceinline__ void cell_update(const Params &p, const Planes &pl, c
     }
 
     // ---- the population loads
+    const Codec<T> ch{p.h_ref, 1.0f, 1.0f}, cg{0.0f, p.g_scale, p.g_inv_scale};
     float gv[QG], hv[15];
     if (active) {
         if (HYDRO) {
 #pragma unroll
-            for (int i = 0; i < QG; ++i) gv[i] = pop_load<QG, G_SW, EDGE>(pl.g, n, i);
+            for (int i = 0; i < QG; ++i) gv[i] = pop_load<T, QG, G_SW, EDGE>(pl.g, n, i, cg);
         }
 #pragma unroll
-        for (int i = 0; i < 15; ++i) hv[i] = pop_load<15, H_SW, EDGE>(pl.h, n, i);
+        for (int i = 0; i < 15; ++i) hv[i] = pop_load<T, 15, H_SW, EDGE>(pl.h, n, i, ch);
     }
 
 #pragma unroll
@@ -259,10 +319,10 @@ __device__ __forceinline__ void cell_update(const Params &p, const Planes &pl, c
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx)
                 nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
-    collide_and_store<QG, G_SW, H_SW, HYDRO, EDGE>(p, pl, n, gv, hv, nb, phi_out, flag);
+    collide_and_store<T, QG, G_SW, H_SW, HYDRO, EDGE>(p, pl, n, gv, hv, nb, phi_out, flag);
 }
 
-template <int QG, bool G_SW, bool H_SW, bool HYDRO>
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO>
 __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
     fused_step_kernel(Params p, Planes pl, const float *__restrict__ phi_in, float *__restrict__ phi_out,
                       int *__restrict__ flag) {
@@ -294,37 +354,54 @@ __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
                       (wy && (blockIdx.y == 0 || (blockIdx.y + 1) * TY >= p.ny)) ||
                       (wz && (blockIdx.z == 0 || (blockIdx.z + 1) * TZ >= p.nz));
     if (edge)
-        cell_update<QG, G_SW, H_SW, HYDRO, true>(p, pl, n, active, phi_in, tile, phi_out, flag);
+        cell_update<T, QG, G_SW, H_SW, HYDRO, true>(p, pl, n, active, phi_in, tile, phi_out, flag);
     else
-        cell_update<QG, G_SW, H_SW, HYDRO, false>(p, pl, n, active, phi_in, tile, phi_out, flag);
+        cell_update<T, QG, G_SW, H_SW, HYDRO, false>(p, pl, n, active, phi_in, tile, phi_out, flag);
 }
 
-template <int QG, bool G_SW, bool H_SW, bool HYDRO>
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO>
 static cudaError_t launch(const Params &p, const Planes &pl, const float *pi, float *po, int *flag,
                           cudaStream_t st) {
     const dim3 block(TX, TY, TZ);
     const dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + TZ - 1) / TZ);
-    fused_step_kernel<QG, G_SW, H_SW, HYDRO><<<grid, block, 0, st>>>(p, pl, pi, po, flag);
+    fused_step_kernel<T, QG, G_SW, H_SW, HYDRO><<<grid, block, 0, st>>>(p, pl, pi, po, flag);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const Params &p, int q_hydro, bool g_sw, bool h_sw, bool hydro, float *h, float *g,
-                        const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
+template <typename T>
+static cudaError_t launch_typed(const Params &p, const Storage &sto, int q_hydro, bool g_sw, bool h_sw, bool hydro,
+                                const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
     Planes pl;
-    for (int i = 0; i < 15; ++i) pl.h[i] = h + (size_t)i * p.N;
-    for (int i = 0; i < 27; ++i) pl.g[i] = i < q_hydro ? g + (size_t)i * p.N : nullptr;
+    pl.h[0] = sto.h.rest;
+    for (int i = 1; i < 15; ++i) pl.h[i] = static_cast<T *>(sto.h.mov) + (size_t)(i - 1) * p.N;
+    pl.g[0] = sto.g.rest;
+    for (int i = 1; i < 27; ++i) pl.g[i] = i < q_hydro ? static_cast<T *>(sto.g.mov) + (size_t)(i - 1) * p.N : nullptr;
     if (!hydro) {
         if (h_sw) return cudaErrorInvalidValue;  // the first phase step starts from natural h
-        return launch<19, false, false, false>(p, pl, phi_in, phi_out, flag, st);
+        return launch<T, 19, false, false, false>(p, pl, phi_in, phi_out, flag, st);
     }
     if (g_sw == h_sw) return cudaErrorInvalidValue;  // h runs one AA step ahead of g
     if (q_hydro == 19)
-        return g_sw ? launch<19, true, false, true>(p, pl, phi_in, phi_out, flag, st)
-                    : launch<19, false, true, true>(p, pl, phi_in, phi_out, flag, st);
+        return g_sw ? launch<T, 19, true, false, true>(p, pl, phi_in, phi_out, flag, st)
+                    : launch<T, 19, false, true, true>(p, pl, phi_in, phi_out, flag, st);
     if (q_hydro == 27)
-        return g_sw ? launch<27, true, false, true>(p, pl, phi_in, phi_out, flag, st)
-                    : launch<27, false, true, true>(p, pl, phi_in, phi_out, flag, st);
+        return g_sw ? launch<T, 27, true, false, true>(p, pl, phi_in, phi_out, flag, st)
+                    : launch<T, 27, false, true, true>(p, pl, phi_in, phi_out, flag, st);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step(const Params &p, const Storage &sto, int q_hydro, bool g_sw, bool h_sw, bool hydro,
+                        const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
+    switch (sto.precision) {
+        case LBM_PRECISION_FP32:
+            return launch_typed<float>(p, sto, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
+        case LBM_PRECISION_FP16:
+            return launch_typed<__half>(p, sto, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
+        case LBM_PRECISION_BF16:
+            return launch_typed<__nv_bfloat16>(p, sto, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
+        default:
+            return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace lbm

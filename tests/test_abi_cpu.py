@@ -66,6 +66,16 @@ def test_workspace_size(lbm):
     assert n27 >= (15 + 27 + 2) * 512 ** 3 * 4  # 23.6 GB at 512^3
 
 
+def test_workspace_size_16bit(lbm):
+    d = lbm.make_domain(64, 64, 64, q_hydro=27)
+    n32 = lbm.lbm_workspace_size(d, lbm.make_params())
+    n16 = lbm.lbm_workspace_size(d, lbm.make_params(precision=lbm.LBM_PRECISION_FP16, store_g_scale=4096.0))
+    N = 64 ** 3
+    # rest planes FP32 (2 x 4 B), moving planes 2 B (14 + 26), two phi planes
+    assert n16 >= (2 * 4 + 40 * 2 + 2 * 4) * N and n16 < (2 * 4 + 40 * 2 + 2 * 4) * N + 200000
+    assert n16 < 0.6 * n32
+
+
 @pytest.mark.parametrize("field,value", [
     ("nx", 0), ("ny", -3), ("q_phase", 19), ("q_hydro", 15), ("q_hydro", 9), ("wall", 2),
 ])
@@ -84,6 +94,7 @@ def test_invalid_domain_rejected(lbm, field, value):
 @pytest.mark.parametrize("field,value", [
     ("rho_H", 0.0), ("rho_ratio", -1.0), ("nu_H", 0.0), ("mu_ratio", 0.0), ("sigma", -1e-4), ("xi", 0.0),
     ("mobility", 0.0), ("rho_ref", float("nan")), ("precision", 7), ("nu_H", float("inf")),
+    ("store_g_scale", 3.0), ("store_g_scale", -4.0), ("store_phi_ref", float("inf")), ("clamp_phi", 2),
 ])
 def test_invalid_params_rejected(lbm, field, value):
     p = lbm.make_params()

@@ -53,6 +53,8 @@ class Problem:
     gravity: tuple = (0.0, 0.0, 0.0)
     rho_ref: float = 1.0
     clamp_phi: int = 0  # 1: phi clamped to [0, 1] inside rho and tau
+    precision: str = "fp32"  # population storage: "fp32", "fp16", "bf16"
+    store_phi_ref: float = 0.0  # 16-bit storage keeps h_i - w_i store_phi_ref (1: mostly heavy fluid)
 
     @property
     def rho_L(self) -> float:
@@ -208,7 +210,7 @@ def rising_bubble(nx: int = 128, ny: int = 512, nz: int = 128, D: float = 32.0, 
     g, sigma, nu_H = _bubble_params(D, Eo, Mo, t_ref)
     prob = Problem(nx, ny, nz, wall=(1, 1, 1), q_hydro=q_hydro, rho_H=1.0, rho_ratio=1000.0, nu_H=nu_H,
                    mu_ratio=100.0, sigma=sigma, xi=5.0, mobility=0.04, gravity=(0.0, -g, 0.0), rho_ref=1.0,
-                   clamp_phi=1)
+                   clamp_phi=1, store_phi_ref=1.0)
     if centre is None:
         centre = (nx / 2, 2 * D, nz / 2)
     phi0 = sphere_phi(prob, centre, D / 2, heavy_inside=False)
@@ -223,7 +225,8 @@ def roofline(n: int = 512, count: int = 400, dmin: float = 16.0, dmax: float = 3
     sigma, Eo, D_ref = 1e-4, 10.0, 24.0
     g = Eo * sigma / (1.0 * D_ref * D_ref)
     prob = Problem(n, n, n, wall=(0, 0, 0), q_hydro=27, rho_H=1.0, rho_ratio=1000.0, nu_H=0.01,
-                   mu_ratio=100.0, sigma=sigma, xi=5.0, mobility=0.02, gravity=(0.0, -g, 0.0), clamp_phi=1)
+                   mu_ratio=100.0, sigma=sigma, xi=5.0, mobility=0.02, gravity=(0.0, -g, 0.0), clamp_phi=1,
+                   store_phi_ref=1.0)
     bubbles = place_bubbles(prob, count, dmin, dmax, seed)
     phi0 = many_bubbles_phi(prob, bubbles).astype(np.float32)
     # buoyancy reference: the mean density, so a periodic gravity axis carries no net force
