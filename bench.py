@@ -214,6 +214,71 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_steps(sim, stream, steps: int) -> float:
+    """Milliseconds for `steps` launches on the library's stream (CUDA events)."""
+    import torch
+
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    sim.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def precision_forms(args, prob, phi0_dev, stream, peak):
+    """The FP16 and BF16 storage forms on the same workload and GPU (timing), and
+    the accuracy of every form on a 64^3 walled rising bubble after 1000 steps
+    against the FP64 oracle (phi L-infinity, rise velocity, mass drift)."""
+    import torch
+
+    from paper_2012_06144_gb300 import lbm
+
+    out = {}
+    steps = min(args.steps, 500)
+    for prec in ("fp16", "bf16"):
+        sim = lbm.Simulation.from_problem(prob, precision=prec, stream=stream)
+        sim.init_phase(phi0_dev)
+        sim.step(args.warmup)
+        sim.synchronize()
+        ms = time_steps(sim, stream, steps) / steps
+        sim.synchronize()
+        bpc = bytes_per_cell(prob.q_hydro, prec)
+        out[prec] = {"value": prob.ncells / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+                     "bytes_per_cell": bpc, "roofline_frac": prob.ncells * bpc / (ms / 1e3) / 1e9 / peak}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    if args.no_accuracy:
+        return out
+    import oracle
+
+    oracle.build()
+    case, phi0 = W.precision_bubble()
+    n = 1000
+    ref = oracle.State(oracle.make_problem(case), phi0).run(n)
+    rphi, ru, _ = ref.fields()
+
+    def rise(phi, u):
+        lf = 1.0 - phi
+        return float((u[1] * lf).sum() / lf.sum())
+
+    acc = {"case": "64^3 walled rising bubble D=16, Eo 10, Mo 1e-3, t_ref 1000, 1000 steps, vs FP64 oracle"}
+    for prec in ("fp32", "fp16", "bf16"):
+        sim = lbm.Simulation.from_problem(case, precision=prec, stream=stream)
+        sim.init_phase(phi0)
+        sim.step(n)
+        sim.synchronize()
+        phi, u, _ = (t.cpu().numpy().astype(np.float64) for t in sim.fields())
+        acc[prec] = {"phi_linf": float(np.abs(phi - rphi).max()),
+                     "rise_velocity_rel": abs(rise(phi, u) - rise(rphi, ru)) / abs(rise(rphi, ru)),
+                     "mass_drift": float(abs(phi.sum() - rphi.sum()) / rphi.sum())}
+        sim.close()
+    out["accuracy"] = acc
+    return out
+
+
 def max_over_ranks(x: float, world: int, device=None) -> float:
     """Largest value of x over all ranks (the slowest rank's time)."""
     if world <= 1:
@@ -243,6 +308,8 @@ def main():
                     help="population storage format (arithmetic is FP32)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP16/BF16 storage forms")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy of the storage forms")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -331,6 +398,11 @@ def main():
             "kernel": f"fused_step_kernel<{args.precision}, 27>", "algorithmic_bytes_per_cell": bytes_per_cell(q, args.precision),
             "launch_ms": launch_ms}
 
+    sim.close()
+    forms = None
+    if rank == 0 and not args.no_precision and args.precision == "fp32" and args.workload == "roofline":
+        forms = precision_forms(args, prob, phi0_dev, stream, peak)
+
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline()
         line = {
@@ -343,10 +415,9 @@ def main():
                              "no flush needed",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps, "precision_forms": forms,
         }
         print(json.dumps(line), flush=True)
-    sim.close()
     if world > 1:
         dist.destroy_process_group()
 
