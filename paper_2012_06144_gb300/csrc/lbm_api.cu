@@ -10,27 +10,7 @@
 #include <new>
 #include <string>
 
-#include "lbm.h"
-#include "lbm_internal.h"
-
-struct lbm_t {
-    lbm_domain dom;
-    lbm_params prm;
-    lbm::Params kp;
-    cudaStream_t stream;
-    int device;
-    char *ws;
-    size_t ws_bytes;
-    bool owns_ws;
-    lbm::Storage sto;
-    float *phi[2];
-    int *flag;
-    double *red_scratch, *red_out;
-    int cur;      // phi[cur] holds phi^t
-    int64_t t;    // time level: steps advanced since initialisation
-    bool ready;   // a state exists
-    std::string err;
-};
+#include "lbm_handle.h"
 
 namespace {
 

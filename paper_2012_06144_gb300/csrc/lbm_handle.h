@@ -1,0 +1,36 @@
+// lbm_handle.h -- the simulation handle behind the opaque lbm_t of the C ABI
+// (shared by the single-simulation entry points and the batch).
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+struct lbm_t {
+    lbm_domain dom;
+    lbm_params prm;
+    lbm::Params kp;
+    cudaStream_t stream;
+    int device;
+    char *ws;
+    size_t ws_bytes;
+    bool owns_ws;
+    lbm::Storage sto;
+    float *phi[2];
+    int *flag;
+    double *red_scratch, *red_out;
+    int cur;      // phi[cur] holds phi^t
+    int64_t t;    // time level: steps advanced since initialisation
+    bool ready;   // a state exists
+    std::string err;
+};
+
+namespace lbm {
+// Bookkeeping of one time step advanced by a launch made elsewhere (the batch).
+inline void advance_level(lbm_t *s) {
+    s->cur ^= 1;
+    s->t += 1;
+}
+}  // namespace lbm

@@ -1,0 +1,368 @@
+// lbm_step_impl.cuh -- device implementation of the fused coupled step, shared
+// by the single-simulation kernel (lbm_step.cu) and the batched kernel
+// (lbm_batch.cu).  See lbm_step.cu for the method and the layout of the work.
+#pragma once
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+#ifndef LBM_MIN_BLOCKS
+#define LBM_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for
+#endif
+
+#ifndef LBM_TY
+#define LBM_TY 4  // default tile: 32 x LBM_TY x LBM_TZ cells per block
+#endif
+#ifndef LBM_TZ
+#define LBM_TZ 2
+#endif
+#ifndef LBM_STREAM_HINTS
+#define LBM_STREAM_HINTS 1  // 1: populations move with evict-first (.cs) loads and stores
+#endif
+
+constexpr int TX = 32;  // one warp = 32 consecutive x
+
+// Plane pointers of both lattices: slot 0 (rest) is FP32, slots >= 1 hold the
+// moving populations in the storage type of the launch.
+struct Planes {
+    void *h[15];
+    void *g[27];
+};
+
+// Plane addresses of one lattice from a table of pointers (kernel parameters).
+struct TableLat {
+    void *const *t;
+    template <typename U>
+    __device__ __forceinline__ U *ptr(int s) const {
+        return static_cast<U *>(t[s]);
+    }
+};
+
+// Plane addresses of one lattice from its rest plane and first moving plane
+// (moving planes N elements apart).
+template <typename T>
+struct BaseLat {
+    float *rest;
+    T *mov;
+    long long N;
+    template <typename U>
+    __device__ __forceinline__ U *ptr(int s) const {
+        if (s == 0) return reinterpret_cast<U *>(rest);
+        return reinterpret_cast<U *>(mov + (size_t)(s - 1) * N);
+    }
+};
+
+// Per-thread neighbour offsets: element index of (x+dx, y+dy, z+dz) is
+// X[dx+1] + Y[dy+1] + Z[dz+1] (X includes the cell's own index).
+struct Nb3 {
+    int X[3], Y[3], Z[3];
+    int lo, hi;  // walled faces touched by this cell (bit a: axis a)
+};
+
+__device__ __forceinline__ int nidx(const Nb3 &n, int dx, int dy, int dz) {
+    return n.X[dx + 1] + n.Y[dy + 1] + n.Z[dz + 1];
+}
+
+__device__ __forceinline__ bool leaves3(const Nb3 &n, V3 e, int sign) {
+    const int ex = e.x * sign, ey = e.y * sign, ez = e.z * sign;
+    return (ex > 0 && (n.hi & 1)) || (ex < 0 && (n.lo & 1)) || (ey > 0 && (n.hi & 2)) || (ey < 0 && (n.lo & 2)) ||
+           (ez > 0 && (n.hi & 4)) || (ez < 0 && (n.lo & 4));
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_pop(const T *a) {
+#if LBM_STREAM_HINTS
+    return __ldcs(a);
+#else
+    return *a;
+#endif
+}
+
+template <typename T>
+__device__ __forceinline__ void st_pop(T *a, T v) {
+#if LBM_STREAM_HINTS
+    __stcs(a, v);
+#else
+    *a = v;
+#endif
+}
+
+// Storage of the moving populations of one lattice in type T: the stored value q
+// decodes as w_i ref + q inv_scale and encodes as (f - w_i ref) scale.
+template <typename T>
+struct Codec {
+    float ref, scale, inv_scale;
+    template <int Q>
+    __device__ __forceinline__ float decode(T q, int i) const {
+        if constexpr (std::is_same<T, float>::value) return q;
+        else return fmaf(to_f(q), inv_scale, wgt<Q>(i) * ref);
+    }
+    template <int Q>
+    __device__ __forceinline__ T encode(float f, int i) const {
+        if constexpr (std::is_same<T, float>::value) return f;
+        else return from_f<T>((f - wgt<Q>(i) * ref) * scale);
+    }
+};
+
+// (slot, element) holding the pre-collision f_i(x) in the AA layout (see lbm_device.cuh)
+template <int Q, bool SW, bool EDGE>
+__device__ __forceinline__ void src_loc(const Nb3 &n, int i, int &slot, int &idx) {
+    if (!SW) {
+        slot = i;
+        idx = n.X[1];
+        return;
+    }
+    const V3 e = vel<Q>(i);
+    if (EDGE && leaves3(n, e, -1)) {
+        slot = i;
+        idx = n.X[1];
+        return;
+    }
+    slot = opp(i);
+    idx = nidx(n, -e.x, -e.y, -e.z);
+}
+
+// (slot, element) that receives the post-collision f*_i(x)
+template <int Q, bool SW, bool EDGE>
+__device__ __forceinline__ void dst_loc(const Nb3 &n, int i, int &slot, int &idx) {
+    if (!SW) {
+        slot = opp(i);
+        idx = n.X[1];
+        return;
+    }
+    const V3 e = vel<Q>(i);
+    if (EDGE && leaves3(n, e, +1)) {
+        slot = opp(i);
+        idx = n.X[1];
+        return;
+    }
+    slot = i;
+    idx = nidx(n, e.x, e.y, e.z);
+}
+
+template <typename T, int Q, bool SW, bool EDGE, typename L>
+__device__ __forceinline__ float pop_load(const L &lat, const Nb3 &n, int i, const Codec<T> &cd) {
+    int slot, idx;
+    src_loc<Q, SW, EDGE>(n, i, slot, idx);
+    if (slot == 0) return ld_pop(lat.template ptr<float>(0) + idx);
+    return cd.template decode<Q>(ld_pop(lat.template ptr<T>(slot) + idx), i);
+}
+
+// stores the rest population (i = 0, FP32) or an encoded moving population
+template <typename T, int Q, bool SW, bool EDGE, typename L>
+__device__ __forceinline__ void pop_store_rest(const L &lat, const Nb3 &n, float v) {
+    int slot, idx;
+    dst_loc<Q, SW, EDGE>(n, 0, slot, idx);
+    st_pop(lat.template ptr<float>(0) + idx, v);
+}
+
+template <typename T, int Q, bool SW, bool EDGE, typename L>
+__device__ __forceinline__ void pop_store_enc(const L &lat, const Nb3 &n, int i, T q) {
+    int slot, idx;
+    dst_loc<Q, SW, EDGE>(n, i, slot, idx);
+    st_pop(lat.template ptr<T>(slot) + idx, q);
+}
+
+// Collision of both lattices at one cell and the streaming stores, from the
+// pre-collision populations gv (g^{k-1}), hv (h^k) and the 3x3x3 neighbourhood nb
+// of phi^{k-1}.
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE, typename LH, typename LG>
+__device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh, const LG &lg, const Nb3 &n, const float *gv,
+                                                  const float *hv, const float *nb, float *__restrict__ phi_out,
+                                                  int *__restrict__ flag) {
+    const Codec<T> ch{p.h_ref, 1.0f, 1.0f}, cg{0.0f, p.g_scale, p.g_inv_scale};
+    const float phic = nb[13];
+    const Stencil S = stencil_sums(nb);
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+
+    // ---- hydrodynamic step k-1 (Section 3.2)
+    if (HYDRO) {
+        Hydro<QG> Hd;
+        hydro_macro<QG>(p, gv, phic, S, Hd);
+        const HydroPost<QG> P = hydro_post<QG>(Hd);
+        // The rest population takes p* - sum_{i>0} g*_i, with each g*_i as the next
+        // reader will decode it, so the stored populations keep the zeroth moment
+        // p* of eq:improved_collision to rounding (the FP32 weights do not sum to 1).
+        float gsum = 0.f;
+#pragma unroll
+        for (int i = 1; i < QG; i += 2) {
+            float E, O;
+            hydro_gstar_pair<QG>(P, i, E, O);
+            const T qa = cg.template encode<QG>(E + O, i), qb = cg.template encode<QG>(E - O, i + 1);
+            pop_store_enc<T, QG, G_SW, EDGE>(lg, n, i, qa);
+            pop_store_enc<T, QG, G_SW, EDGE>(lg, n, i + 1, qb);
+            gsum += cg.template decode<QG>(qa, i) + cg.template decode<QG>(qb, i + 1);
+        }
+        pop_store_rest<T, QG, G_SW, EDGE>(lg, n, Hd.pstar - gsum);
+        ux = Hd.ux;
+        uy = Hd.uy;
+        uz = Hd.uz;
+        if (!(fabsf(Hd.pstar) < 1e30f)) *flag = 1;
+    }
+
+    // ---- phase-field step k (Section 3.1)
+    // phi_k = sum_i h_i (eq:updatePhaseField), summed as a tree over opposite pairs
+    float pr[8];
+    pr[0] = hv[0];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) pr[j + 1] = hv[2 * j + 1] + hv[2 * j + 2];
+    const float phik = ((pr[0] + pr[1]) + (pr[2] + pr[3])) + ((pr[4] + pr[5]) + (pr[6] + pr[7]));
+    phi_out[n.X[1]] = phik;
+    if (!(fabsf(phik) < 1e30f)) *flag = 1;
+
+    // interface normal from eq:grad with D3Q15 weights (the face and corner sums
+    // of the same neighbourhood)
+    float Gx, Gy, Gz;
+    stencil_grad<15>(S, Gx, Gy, Gz);
+    const float G2 = Gx * Gx + Gy * Gy + Gz * Gz;
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    if (G2 > 1e-24f) {
+        float inv = rsqrtf(G2);
+        inv = inv * (1.5f - 0.5f * G2 * inv * inv);  // one Newton step: no systematic bias in |n|
+        nx = Gx * inv;
+        ny = Gy * inv;
+        nz = Gz * inv;
+    }
+    const float pc = phic - 0.5f;
+    const float theta = (1.0f - 4.0f * pc * pc) * p.inv_xi;
+    const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float om = p.omega_phi, fc = 1.0f - 0.5f * om;
+    // h*_i = h_i + omega (h^eq_i - h_i - F_i/2) + F_i over opposite pairs, with
+    // h^eq = phi_k w (1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u) and F_i = theta w e.n.
+    // The non-equilibrium h^eq_i - h_i is formed as fma(phi_k, w, -h_i) + phi_k w
+    // (velocity terms), so it carries no rounding of the large product phi w.
+    // The rest population takes h_0 - sum_{i>0} (h*_i - h_i), with each h*_i as
+    // the next reader will decode it: each increment is exact in FP32 (h*_i and
+    // h_i are close), so the stored populations sum to the incoming sum_i h_i up
+    // to the rounding of small increments, i.e. the cell's phase mass is kept.
+    float dsum = 0.f;
+#pragma unroll
+    for (int i = 1; i < 15; i += 2) {
+        const V3 e = vel<15>(i);
+        const float w = wgt<15>(i);
+        const float eu = e.x * ux + e.y * uy + e.z * uz;
+        const float en = e.x * nx + e.y * ny + e.z * nz;
+        const float pw = phik * w;
+        const float x_even = pw * (4.5f * eu * eu - uu);
+        const float x_odd = pw * 3.0f * eu;
+        const float F = fc * (theta * w * en);
+        const float neq_a = fmaf(phik, w, -hv[i]) + (x_even + x_odd);
+        const float neq_b = fmaf(phik, w, -hv[i + 1]) + (x_even - x_odd);
+        const float a = hv[i] + fmaf(om, neq_a, F);
+        const float b = hv[i + 1] + fmaf(om, neq_b, -F);
+        const T qa = ch.template encode<15>(a, i), qb = ch.template encode<15>(b, i + 1);
+        pop_store_enc<T, 15, H_SW, EDGE>(lh, n, i, qa);
+        pop_store_enc<T, 15, H_SW, EDGE>(lh, n, i + 1, qb);
+        dsum += (ch.template decode<15>(qa, i) - hv[i]) + (ch.template decode<15>(qb, i + 1) - hv[i + 1]);
+    }
+    pop_store_rest<T, 15, H_SW, EDGE>(lh, n, hv[0] - dsum);
+}
+
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE, int TY, int TZ, typename LH, typename LG>
+__device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const LG &lg, const Nb3 &n, bool active,
+                                            const float *__restrict__ phi_in, float (*tile)[TY + 2][TX + 2],
+                                            float *__restrict__ phi_out, int *__restrict__ flag, int bx, int by,
+                                            int bz, int tx, int ty, int tz) {
+    constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
+
+    // ---- phi^{k-1} tile with a one-cell halo (wrap on periodic axes, mirror at
+    // walls), filled row by row: warp w loads rows w, w + 8, ... of the HZ x HY
+    // rows, lane l the x-offsets l and (lanes 0, 1) 32 + l.  The loads are issued
+    // before the population loads so that their latency overlaps.
+    constexpr int NROW = HY * HZ, NWARP = TX * TY * TZ / 32, RPW = (NROW + NWARP - 1) / NWARP;
+    const int lane = tx, warp = ty + TY * tz;
+    const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
+    const int gx0 = min(wrap_or_clamp(bx * TX - 1 + lane, p.nx, wx), p.nx - 1);
+    const int gx1 = min(wrap_or_clamp(bx * TX + 31 + lane, p.nx, wx), p.nx - 1);
+    float tv0[RPW], tv1[RPW];
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int r = warp + k * NWARP;
+        if (r < NROW) {
+            const int kz = r / HY, ky = r - kz * HY;
+            // coordinates beyond a ragged box end are clamped into the box; those
+            // halo entries only feed threads that are inactive
+            const int gy = min(wrap_or_clamp(by * TY - 1 + ky, p.ny, wy), p.ny - 1);
+            const int gz = min(wrap_or_clamp(bz * TZ - 1 + kz, p.nz, wz), p.nz - 1);
+            const float *row = phi_in + (size_t)gy * p.nx + (size_t)gz * p.nx * p.ny;
+            tv0[k] = __ldg(row + gx0);
+            if (lane < HX - 32) tv1[k] = __ldg(row + gx1);
+        }
+    }
+
+    // ---- the population loads
+    const Codec<T> ch{p.h_ref, 1.0f, 1.0f}, cg{0.0f, p.g_scale, p.g_inv_scale};
+    float gv[QG], hv[15];
+    if (active) {
+        if (HYDRO) {
+#pragma unroll
+            for (int i = 0; i < QG; ++i) gv[i] = pop_load<T, QG, G_SW, EDGE>(lg, n, i, cg);
+        }
+#pragma unroll
+        for (int i = 0; i < 15; ++i) hv[i] = pop_load<T, 15, H_SW, EDGE>(lh, n, i, ch);
+    }
+
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int r = warp + k * NWARP;
+        if (r < NROW) {
+            const int kz = r / HY, ky = r - kz * HY;
+            tile[kz][ky][lane] = tv0[k];
+            if (lane < HX - 32) tile[kz][ky][32 + lane] = tv1[k];
+        }
+    }
+    __syncthreads();
+    if (!active) return;
+    float nb[27];
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx)
+                nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
+    collide_and_store<T, QG, G_SW, H_SW, HYDRO, EDGE>(p, lh, lg, n, gv, hv, nb, phi_out, flag);
+}
+
+// One tile (bx, by, bz) of 32 x TY x TZ cells, one thread per cell: per-thread
+// neighbour offsets, then the bounce-back-checking path only if the tile touches
+// a walled face.  Every thread of the block must call this (it synchronises).
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, int TY, int TZ, typename LH, typename LG>
+__device__ __forceinline__ void tile_update(const Params &p, const LH &lh, const LG &lg,
+                                            const float *__restrict__ phi_in, float *__restrict__ phi_out,
+                                            int *__restrict__ flag, float (*tile)[TY + 2][TX + 2], int bx, int by,
+                                            int bz, int tx, int ty, int tz) {
+    const int x = bx * TX + tx;
+    const int y = by * TY + ty;
+    const int z = bz * TZ + tz;
+    const bool active = x < p.nx && y < p.ny && z < p.nz;
+
+    const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
+    const int xc = min(x, p.nx - 1), yc = min(y, p.ny - 1), zc = min(z, p.nz - 1);
+    const int nxy = p.nx * p.ny;
+    Nb3 n;
+    const int c = xc + p.nx * yc + nxy * zc;
+    n.X[0] = c + wrap_or_clamp(xc - 1, p.nx, wx) - xc;
+    n.X[1] = c;
+    n.X[2] = c + wrap_or_clamp(xc + 1, p.nx, wx) - xc;
+    n.Y[0] = (wrap_or_clamp(yc - 1, p.ny, wy) - yc) * p.nx;
+    n.Y[1] = 0;
+    n.Y[2] = (wrap_or_clamp(yc + 1, p.ny, wy) - yc) * p.nx;
+    n.Z[0] = (wrap_or_clamp(zc - 1, p.nz, wz) - zc) * nxy;
+    n.Z[1] = 0;
+    n.Z[2] = (wrap_or_clamp(zc + 1, p.nz, wz) - zc) * nxy;
+    n.lo = (wx && xc == 0 ? 1 : 0) | (wy && yc == 0 ? 2 : 0) | (wz && zc == 0 ? 4 : 0);
+    n.hi = (wx && xc == p.nx - 1 ? 1 : 0) | (wy && yc == p.ny - 1 ? 2 : 0) | (wz && zc == p.nz - 1 ? 4 : 0);
+
+    const bool edge = (wx && (bx == 0 || (bx + 1) * TX >= p.nx)) || (wy && (by == 0 || (by + 1) * TY >= p.ny)) ||
+                      (wz && (bz == 0 || (bz + 1) * TZ >= p.nz));
+    if (edge)
+        cell_update<T, QG, G_SW, H_SW, HYDRO, true, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+                                                            by, bz, tx, ty, tz);
+    else
+        cell_update<T, QG, G_SW, H_SW, HYDRO, false, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+                                                             by, bz, tx, ty, tz);
+}
+
+}  // namespace lbm
