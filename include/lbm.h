@@ -172,6 +172,69 @@ const char *lbm_last_error(const lbm_t *s);
 /* Releases the handle and, if the library allocated it, the workspace. */
 void lbm_destroy(lbm_t *s);
 
+/* ---- Batched stepping: many independent simulations advanced together -----
+ *
+ * A batch advances several independent problems (their own sizes, walls and
+ * Section 3 parameters; one hydrodynamic lattice for all) by the coupled step
+ * of Algorithm 2, each exactly as lbm_step would advance it alone: one launch
+ * per time step (per group of up to 64 members) runs one thread block per entry
+ * of a table of the members' 32 x TY x TZ cell tiles.  Aimed at parameter
+ * sweeps of small boxes, which alone cannot fill the GPU.
+ *
+ * Members are ordinary lbm_t handles owned by the batch (lbm_batch_member):
+ * initialise them with lbm_init_phase or lbm_set_state, read them with
+ * lbm_get_fields, lbm_reduce, lbm_get_state; do not lbm_step or lbm_destroy
+ * them.  All members must be at the same time level when the batch steps
+ * (LBM_ERR_STATE otherwise).  FP32 population storage only. */
+typedef struct lbm_batch_t lbm_batch_t; /* opaque batch handle */
+
+/* Device workspace for the batch's members: the sum over members of
+ * lbm_workspace_size, each rounded up to a multiple of 256 bytes.  Host-only. */
+lbm_status lbm_batch_workspace_size(int count, const lbm_domain *doms, const lbm_params *prms, size_t *bytes);
+
+/* Creates a batch of count (1..65536) members from count domains and
+ * parameter sets (validated as by lbm_create; every q_hydro equal and every
+ * precision LBM_PRECISION_FP32, else LBM_ERR_ARG) on the current CUDA device.
+ * cuda_stream: stream for all of the batch's work (members included), NULL for
+ * the legacy default stream (then no CUDA graphs are used).  workspace: device
+ * buffer of lbm_batch_workspace_size() bytes, 256-byte aligned, owned by the
+ * caller until lbm_batch_destroy; or NULL to let each member allocate its own.
+ * The batch itself allocates its member and tile tables (a few bytes per tile).
+ * Errors of this call read as lbm_last_error(NULL). */
+lbm_status lbm_batch_create(lbm_batch_t **out, int count, const lbm_domain *doms, const lbm_params *prms,
+                            void *cuda_stream, void *workspace, size_t workspace_bytes);
+
+/* Number of members (0 for NULL). */
+int lbm_batch_size(const lbm_batch_t *b);
+
+/* Member i (0-based) of the batch, or NULL if i is out of range.  The handle
+ * stays owned by the batch. */
+lbm_t *lbm_batch_member(lbm_batch_t *b, int i);
+
+/* Advances every member by n >= 0 coupled time steps.  Asynchronous.  On a
+ * non-default stream, runs of 16 steps are replayed from CUDA graphs captured
+ * on first use (so the first call of a run may take longer). */
+lbm_status lbm_batch_step(lbm_batch_t *b, int64_t n);
+
+/* Autotuner: for each of 3 tile shapes (TY, TZ) = (4, 2), (8, 1), (2, 4) and
+ * each of 2 table orders (0: member after member; 1: members' tiles dealt out
+ * round robin) runs 1 + trial_steps batched steps, times the trial steps with
+ * CUDA events, and keeps the fastest pair.  The trial steps are real time
+ * steps: every member advances by 6 (1 + trial_steps).  choice (may be NULL)
+ * receives shape * 2 + order of the winner; ms_per_step (may be NULL) receives
+ * the 6 measured times in the same order.  Synchronises the stream. */
+lbm_status lbm_batch_tune(lbm_batch_t *b, int trial_steps, int *choice, double *ms_per_step);
+
+/* lbm_synchronize on every member: LBM_ERR_DIVERGED if any member produced a
+ * non-finite phi or p* (lbm_last_error on that member says which). */
+lbm_status lbm_batch_synchronize(lbm_batch_t *b);
+
+/* Text of the last failure of a batch call on b. */
+const char *lbm_batch_last_error(const lbm_batch_t *b);
+
+/* Releases the batch, its members and whatever they allocated. */
+void lbm_batch_destroy(lbm_batch_t *b);
+
 /* The LBM_DIAG_* diagnostics of a state that the caller holds in device memory,
  * computed without allocating any device memory.  The paper has no counterpart:
  * this serves callers that cannot allocate at this point -- a host application

@@ -67,7 +67,20 @@ _SIGNATURES = {
     "lbm_destroy": ([_VP], None),
     "lbm_reduce_state_noalloc": ([ctypes.POINTER(lbm_domain), ctypes.POINTER(lbm_params), _FP, _FP, _DP, _VP],
                                  ctypes.c_int),
+    "lbm_batch_workspace_size": ([ctypes.c_int, ctypes.POINTER(lbm_domain), ctypes.POINTER(lbm_params),
+                                  ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "lbm_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(lbm_domain),
+                          ctypes.POINTER(lbm_params), _VP, _VP, ctypes.c_size_t], ctypes.c_int),
+    "lbm_batch_size": ([_VP], ctypes.c_int),
+    "lbm_batch_member": ([_VP, ctypes.c_int], _VP),
+    "lbm_batch_step": ([_VP, ctypes.c_int64], ctypes.c_int),
+    "lbm_batch_tune": ([_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP], ctypes.c_int),
+    "lbm_batch_synchronize": ([_VP], ctypes.c_int),
+    "lbm_batch_last_error": ([_VP], ctypes.c_char_p),
+    "lbm_batch_destroy": ([_VP], None),
 }
+BATCH_SHAPES = [(4, 2), (8, 1), (2, 4)]  # (TY, TZ) of the autotuner's tile shapes, in its order
+BATCH_ORDERS = ["member", "round_robin"]
 
 
 def header_functions() -> list:
@@ -100,6 +113,12 @@ def load():
 def _check(status: int, handle=None):
     if status != LBM_OK:
         msg = load().lbm_last_error(handle)
+        raise LBMError(status, msg.decode() if msg else "")
+
+
+def _check_batch(status: int, b):
+    if status != LBM_OK:
+        msg = load().lbm_batch_last_error(b)
         raise LBMError(status, msg.decode() if msg else "")
 
 
@@ -205,6 +224,63 @@ def lbm_reduce_state_noalloc(dom: lbm_domain, prm: lbm_params, g: int, phi: int,
     return out
 
 
+def _arrays(doms, prms):
+    n = len(doms)
+    if n != len(prms) or n < 1:
+        raise ValueError("need as many parameter sets as domains, at least one")
+    return n, (lbm_domain * n)(*doms), (lbm_params * n)(*prms)
+
+
+def lbm_batch_workspace_size(doms, prms) -> int:
+    n, da, pa = _arrays(doms, prms)
+    out = ctypes.c_size_t(0)
+    _check(load().lbm_batch_workspace_size(n, da, pa, ctypes.byref(out)))
+    return out.value
+
+
+def lbm_batch_create(doms, prms, stream: int = 0, workspace: int = 0, workspace_bytes: int = 0):
+    n, da, pa = _arrays(doms, prms)
+    b = ctypes.c_void_p()
+    _check(load().lbm_batch_create(ctypes.byref(b), n, da, pa, stream or None, workspace or None, workspace_bytes))
+    return b
+
+
+def lbm_batch_size(b) -> int:
+    return int(load().lbm_batch_size(b))
+
+
+def lbm_batch_member(b, i: int):
+    h = load().lbm_batch_member(b, int(i))
+    if not h:
+        raise IndexError(f"batch has no member {i}")
+    return ctypes.c_void_p(h)
+
+
+def lbm_batch_step(b, n: int):
+    _check_batch(load().lbm_batch_step(b, int(n)), b)
+
+
+def lbm_batch_tune(b, trial_steps: int = 5):
+    """(choice, ms_per_step[6]) -- choice = shape * 2 + order."""
+    choice = ctypes.c_int(-1)
+    ms = np.zeros(len(BATCH_SHAPES) * len(BATCH_ORDERS))
+    _check_batch(load().lbm_batch_tune(b, int(trial_steps), ctypes.byref(choice), ms.ctypes.data_as(_DP)), b)
+    return choice.value, ms
+
+
+def lbm_batch_synchronize(b):
+    _check_batch(load().lbm_batch_synchronize(b), b)
+
+
+def lbm_batch_last_error(b) -> str:
+    m = load().lbm_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def lbm_batch_destroy(b):
+    load().lbm_batch_destroy(b)
+
+
 # ---- convenience wrapper: device memory and stream from PyTorch --------------------------------------
 
 
@@ -212,10 +288,19 @@ class Simulation:
     """One simulation on the current CUDA device.  Workspace = a torch uint8
     tensor; all work goes to torch's current stream (or ``stream``)."""
 
-    def __init__(self, domain: lbm_domain, params: lbm_params, stream=None, device=None):
+    def __init__(self, domain: lbm_domain, params: lbm_params, stream=None, device=None, _member_of=None):
         import torch
 
         self.torch = torch
+        if _member_of is not None:  # a member of a Batch: the batch owns handle and memory
+            batch, i = _member_of
+            self.domain, self.params, self.device, self.stream = domain, params, batch.device, batch.stream
+            self._batch = batch
+            self.handle = lbm_batch_member(batch.handle, i)
+            self.shape = (domain.nz, domain.ny, domain.nx)
+            self.N = domain.nx * domain.ny * domain.nz
+            return
+        self._batch = None
         self.domain, self.params = domain, params
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.nbytes = lbm_workspace_size(domain, params)
@@ -234,6 +319,9 @@ class Simulation:
         return cls(d, p, **kw)
 
     def close(self):
+        if getattr(self, "_batch", None) is not None:  # members go with their batch
+            self.handle = None
+            return
         if getattr(self, "handle", None):
             lbm_destroy(self.handle)
             self.handle = None
@@ -308,3 +396,61 @@ class Simulation:
             lbm_set_state(self.handle, h.ctypes.data, g.ctypes.data, phi.ctypes.data, 0)
         else:
             lbm_set_state(self.handle, self._dev(h), self._dev(g), self._dev(phi), 1)
+
+
+class Batch:
+    """Independent simulations stepped together (``lbm_batch_*``).  One torch
+    workspace holds every member; ``members[i]`` is a ``Simulation`` view of
+    member i for initialisation and read-back (do not step it on its own)."""
+
+    def __init__(self, domains, params, stream=None, device=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.nbytes = lbm_batch_workspace_size(domains, params)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            aligned = (self.workspace.data_ptr() + 255) & ~255
+            self.handle = lbm_batch_create(domains, params, self.stream.cuda_stream, aligned, self.nbytes)
+        self.members = [Simulation(d, p, _member_of=(self, i)) for i, (d, p) in enumerate(zip(domains, params))]
+        self.cells = sum(d.nx * d.ny * d.nz for d in domains)
+
+    @classmethod
+    def from_problems(cls, problems, **kw):
+        dp = [from_problem(p) for p in problems]
+        return cls([d for d, _ in dp], [p for _, p in dp], **kw)
+
+    def __len__(self):
+        return len(self.members)
+
+    def step(self, n: int = 1):
+        lbm_batch_step(self.handle, n)
+
+    def tune(self, trial_steps: int = 5):
+        """Times every (tile shape, table order) on the batch -- the trial steps
+        advance every member -- and keeps the fastest.  Returns
+        (shape (TY, TZ), order name, ms_per_step for all candidates)."""
+        choice, ms = lbm_batch_tune(self.handle, trial_steps)
+        no = len(BATCH_ORDERS)
+        return BATCH_SHAPES[choice // no], BATCH_ORDERS[choice % no], ms
+
+    def synchronize(self):
+        lbm_batch_synchronize(self.handle)
+
+    def steps_done(self) -> int:
+        return self.members[0].steps_done()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for m in self.members:
+                m.handle = None
+            lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

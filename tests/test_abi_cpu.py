@@ -137,3 +137,49 @@ def test_problem_translation(lbm):
     d, p = lbm.from_problem(prob)
     assert (d.nx, d.ny, d.nz, d.q_hydro, d.q_phase) == (32, 32, 32, 19, 15)
     assert p.rho_ratio == 1000.0 and p.mu_ratio == 100.0 and p.sigma == 1e-4
+
+
+# ---- batch: sizes and validation are host-only ------------------------------------------------------
+
+
+def test_batch_workspace_size_sums_members(lbm):
+    doms = [lbm.make_domain(32, 32, 32, q_hydro=27), lbm.make_domain(5, 3, 2, q_hydro=27),
+            lbm.make_domain(48, 96, 48, q_hydro=27)]
+    prms = [lbm.make_params(), lbm.make_params(rho_ratio=10.0), lbm.make_params(sigma=1e-3)]
+    total = lbm.lbm_batch_workspace_size(doms, prms)
+    each = [lbm.lbm_workspace_size(d, p) for d, p in zip(doms, prms)]
+    assert total == sum((n + 255) // 256 * 256 for n in each)
+
+
+def test_batch_create_rejects_before_cuda(lbm):
+    a, b = lbm.make_domain(8, 8, 8, q_hydro=27), lbm.make_domain(8, 8, 8, q_hydro=19)
+    p = lbm.make_params()
+    cases = [
+        ([a, b], [p, p], lbm.LBM_ERR_ARG),  # mixed hydrodynamic lattices
+        ([a, a], [p, lbm.make_params(precision=lbm.LBM_PRECISION_BF16)], lbm.LBM_ERR_ARG),  # 16-bit storage
+        ([a, lbm.make_domain(0, 8, 8)], [p, p], lbm.LBM_ERR_ARG),  # invalid member
+        ([a, a], [p, lbm.make_params(xi=0.0)], lbm.LBM_ERR_ARG),
+    ]
+    for doms, prms, status in cases:
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_batch_create(doms, prms)
+        assert ei.value.status == status
+        assert lbm.lbm_last_error(None)
+    n = lbm.lbm_batch_workspace_size([a, a], [p, p])
+    with pytest.raises(lbm.LBMError) as ei:  # fake workspace, never dereferenced: rejected first
+        lbm.lbm_batch_create([a, a], [p, p], 0, 256 * 1024, n - 1)
+    assert ei.value.status == lbm.LBM_ERR_OOM
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_batch_create([a, a], [p, p], 0, 256 * 1024 + 16, n)
+    assert ei.value.status == lbm.LBM_ERR_ARG
+
+
+def test_batch_null_handle_calls(lbm):
+    lib = lbm.load()
+    assert lib.lbm_batch_step(None, 1) == lbm.LBM_ERR_ARG
+    assert lib.lbm_batch_tune(None, 1, None, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_batch_synchronize(None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_batch_size(None) == 0
+    assert lib.lbm_batch_member(None, 0) is None
+    assert lib.lbm_batch_last_error(None) == b""
+    lib.lbm_batch_destroy(None)

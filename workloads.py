@@ -221,6 +221,44 @@ def precision_bubble():
     return rising_bubble(64, 64, 64, D=16.0, centre=(32.0, 16.0, 32.0), t_ref=1000.0)
 
 
+BATCH_SIZES = ((32, 32, 32), (48, 96, 48), (64, 128, 64), (96, 192, 96))
+
+
+def _s_nu(nu: float) -> float:
+    return 1.0 / (3.0 * nu + 0.5)
+
+
+def batched(count: int = 64, seed: int = SEED, u_s: float = 0.016, re_gr: float = 30.0):
+    """Independent walled rising-bubble problems for batched stepping.
+
+    Each draw: a box among BATCH_SIZES, density ratio among {10, 100, 1000},
+    Eo ~ U[1, 50]; bubble diameter D = nx / 4 centred in x and z at height y = 2D.
+    With u_s = sqrt(g D) and Re_Gr = rho_H u_s D / mu_H fixed: g = u_s^2 / D,
+    sigma = rho_H g D^2 / Eo, nu_H = u_s D / Re_Gr, viscosity ratio 100.  Draws
+    whose relaxation rate s_nu = 1 / (3 nu + 1/2) leaves (0.05, 1.98) in either
+    fluid are redrawn.  Returns [(Problem, phi0, draw)] with draw = dict(size,
+    rho_ratio, Eo, D)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        size = BATCH_SIZES[int(rng.integers(len(BATCH_SIZES)))]
+        ratio = float((10.0, 100.0, 1000.0)[int(rng.integers(3))])
+        Eo = float(rng.uniform(1.0, 50.0))
+        nx, ny, nz = size
+        D = nx / 4.0
+        g = u_s * u_s / D
+        nu_H = u_s * D / re_gr
+        nu_L = nu_H * ratio / 100.0  # mu_L = mu_H / 100, rho_L = rho_H / ratio
+        if not all(0.05 < _s_nu(nu) < 1.98 for nu in (nu_H, nu_L)):
+            continue
+        prob = Problem(nx, ny, nz, wall=(1, 1, 1), q_hydro=27, rho_H=1.0, rho_ratio=ratio, nu_H=nu_H,
+                       mu_ratio=100.0, sigma=g * D * D / Eo, xi=5.0, mobility=0.04, gravity=(0.0, -g, 0.0),
+                       rho_ref=1.0, clamp_phi=1, store_phi_ref=1.0)
+        phi0 = sphere_phi(prob, (nx / 2, 2 * D, nz / 2), D / 2, heavy_inside=False).astype(np.float32)
+        out.append((prob, phi0, dict(size=size, rho_ratio=ratio, Eo=Eo, D=D)))
+    return out
+
+
 def roofline(n: int = 512, count: int = 400, dmin: float = 16.0, dmax: float = 32.0, seed: int = SEED):
     sigma, Eo, D_ref = 1e-4, 10.0, 24.0
     g = Eo * sigma / (1.0 * D_ref * D_ref)
