@@ -338,6 +338,34 @@ def batched_form(args, stream, peak):
     return out
 
 
+def rising_bubble_form(args, stream):
+    """The walled 128x512x128 rising bubble (D = 32, Eo 10, Mo 1e-3, t_ref 2000)
+    for args.rising_steps steps: light-phase centroid and rise velocity recorded
+    every 100 steps, terminal velocity over the last reference time, drag
+    coefficient and the empirical correlation (Section 6.1)."""
+    import torch
+
+    from paper_2012_06144_gb300 import lbm, observables as O
+
+    prob, phi0 = W.rising_bubble()
+    sim = lbm.Simulation.from_problem(prob, stream=stream)
+    sim.init_phase(phi0)
+    t0 = time.perf_counter()
+    rec = O.track(sim, steps=args.rising_steps, every=100)
+    sim.synchronize()
+    wall = time.perf_counter() - t0
+    out = O.summary(prob, rec, 32.0, window=1.0)
+    t, c, v, _, _ = rec.arrays()
+    k = np.linspace(0, len(t) - 1, 11).astype(int)
+    out.update({"steps": args.rising_steps, "mlups_with_reductions": prob.ncells * args.rising_steps / wall / 1e6,
+                "series_every_tenth": {"t_star": (t[k] / out["t_ref"]).tolist(), "y_c": c[k, 1].tolist(),
+                                       "u_y": v[k, 1].tolist()}})
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return out
+
+
 def max_over_ranks(x: float, world: int, device=None) -> float:
     """Largest value of x over all ranks (the slowest rank's time)."""
     if world <= 1:
@@ -371,6 +399,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true", help="skip the accuracy of the storage forms")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched rising-bubble workload")
     ap.add_argument("--batched-steps", type=int, default=5000, help="timed steps of the batched workload")
+    ap.add_argument("--no-rising", action="store_true", help="skip the rising-bubble observables")
+    ap.add_argument("--rising-steps", type=int, default=10000, help="steps of the rising-bubble run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -466,6 +496,9 @@ def main():
     batched = None
     if rank == 0 and not args.no_batched and args.precision == "fp32" and args.workload == "roofline":
         batched = batched_form(args, stream, peak)
+    rising = None
+    if rank == 0 and not args.no_rising and args.precision == "fp32" and args.workload == "roofline":
+        rising = rising_bubble_form(args, stream)
 
     if rank == 0:
         cpu = None if args.no_cpu_baseline else cpu_baseline()
@@ -480,6 +513,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
             "gpu_launches": args.steps, "precision_forms": forms, "batched_form": batched,
+            "rising_bubble": rising,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

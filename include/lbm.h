@@ -96,17 +96,20 @@ typedef struct {
 } lbm_params;
 
 /* Diagnostics returned by lbm_reduce (FP64 accumulation).  "Light" weights a
- * cell by (1 - phi), the light-phase fraction. */
+ * cell by the bubble indicator b = clamp(1 - 2 phi, 0, 1): 1 in the light phase,
+ * falling to 0 at the interface's mid-level phi = 1/2 and 0 beyond, so that the
+ * heavy bulk -- where acoustic waves move phi by ~1e-4 around 1 over millions
+ * of cells -- does not enter the bubble's centroid and velocity. */
 enum {
     LBM_DIAG_MASS = 0,    /* sum phi                                               */
     LBM_DIAG_MOM_X = 1,   /* sum rho u_x   (rho from eq:density, phi clamped if clamp_phi) */
     LBM_DIAG_MOM_Y = 2,
     LBM_DIAG_MOM_Z = 3,
-    LBM_DIAG_LIGHT_VOL = 4,  /* sum (1 - phi)                                      */
-    LBM_DIAG_LIGHT_X = 5,    /* sum (x + 1/2)(1 - phi) / sum (1 - phi): centroid   */
+    LBM_DIAG_LIGHT_VOL = 4,  /* sum b                                              */
+    LBM_DIAG_LIGHT_X = 5,    /* sum (x + 1/2) b / sum b: centroid                  */
     LBM_DIAG_LIGHT_Y = 6,
     LBM_DIAG_LIGHT_Z = 7,
-    LBM_DIAG_LIGHT_UX = 8,   /* sum u_x (1 - phi) / sum (1 - phi): rise velocity   */
+    LBM_DIAG_LIGHT_UX = 8,   /* sum u_x b / sum b: rise velocity                   */
     LBM_DIAG_LIGHT_UY = 9,
     LBM_DIAG_LIGHT_UZ = 10,
     LBM_DIAG_MAX_U = 11,     /* max |u|                                            */

@@ -231,7 +231,8 @@ __global__ void __launch_bounds__(256) reduce_partial_kernel(Params p, LatView<T
         load_g<T, QG, G_SW>(p, g, C, gv);
         Hydro<QG> H;
         hydro_macro<QG>(p, gv, nb[13], stencil_sums(nb), H);
-        const double f = nb[13], lf = 1.0 - f, rho = H.rho;
+        // bubble indicator: 1 in the light phase, 0 wherever phi >= 1/2
+        const double f = nb[13], lf = fmin(fmax(1.0 - 2.0 * f, 0.0), 1.0), rho = H.rho;
         acc[0] += f;
         acc[1] += rho * H.ux;
         acc[2] += rho * H.uy;

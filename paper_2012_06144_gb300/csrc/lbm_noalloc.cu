@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(kNoAllocThreads) noalloc_partial_kernel(Params
         for (int i = 0; i < QG; ++i) gv[i] = g[pop_src<QG, false>(C, p.N, i)];
         Hydro<QG> H;
         hydro_macro<QG>(p, gv, nb[13], stencil_sums(nb), H);
-        const double f = nb[13], lf = 1.0 - f, rho = H.rho;
+        // bubble indicator: 1 in the light phase, 0 wherever phi >= 1/2
+        const double f = nb[13], lf = fmin(fmax(1.0 - 2.0 * f, 0.0), 1.0), rho = H.rho;
         acc[0] += f;
         acc[1] += rho * H.ux;
         acc[2] += rho * H.uy;
