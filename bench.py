@@ -338,6 +338,40 @@ def batched_form(args, stream, peak):
     return out
 
 
+def unfused_bytes_per_cell(q: int) -> int:
+    """Algorithmic bytes of one unfused step per cell (FP32): hydro collision
+    2q + 1 + 3, phase collision 15 + 15 + 1 + 3 + 1, streaming 2 x 15 and 2 x q."""
+    return 4 * ((2 * q + 4) + 35 + 30 + 2 * q)
+
+
+def unfused_form(args, prob, phi0_dev, stream, peak, fused_ms):
+    """The unfused baseline (Algorithm 1's passes: a collision and a streaming
+    kernel per lattice over two grids) on the same workload and GPU, next to the
+    fused step it is the baseline of."""
+    import torch
+
+    from paper_2012_06144_gb300 import lbm
+
+    d, prm = lbm.from_problem(prob)
+    prm.kernel_form = lbm.LBM_FORM_UNFUSED
+    sim = lbm.Simulation(d, prm, stream=stream)
+    sim.init_phase(phi0_dev)
+    sim.step(args.warmup // 10 + 3)
+    sim.synchronize()
+    steps = min(args.steps, 200)
+    ms = time_steps(sim, stream, steps) / steps
+    sim.synchronize()
+    bpc = unfused_bytes_per_cell(prob.q_hydro)
+    out = {"value": prob.ncells / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "kernels_per_step": 4, "bytes_per_cell": bpc,
+           "roofline_frac": prob.ncells * bpc / (ms / 1e3) / 1e9 / peak,
+           "fused_speedup": ms / fused_ms}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return out
+
+
 def rising_bubble_form(args, stream):
     """The walled 128x512x128 rising bubble (D = 32, Eo 10, Mo 1e-3, t_ref 2000)
     for args.rising_steps steps: light-phase centroid and rise velocity recorded
@@ -400,6 +434,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched rising-bubble workload")
     ap.add_argument("--batched-steps", type=int, default=5000, help="timed steps of the batched workload")
     ap.add_argument("--no-rising", action="store_true", help="skip the rising-bubble observables")
+    ap.add_argument("--no-unfused", action="store_true", help="skip the unfused baseline")
     ap.add_argument("--rising-steps", type=int, default=10000, help="steps of the rising-bubble run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -496,6 +531,9 @@ def main():
     batched = None
     if rank == 0 and not args.no_batched and args.precision == "fp32" and args.workload == "roofline":
         batched = batched_form(args, stream, peak)
+    unfused = None
+    if rank == 0 and not args.no_unfused and args.precision == "fp32" and args.workload == "roofline":
+        unfused = unfused_form(args, prob, phi0_dev, stream, peak, launch_ms)
     rising = None
     if rank == 0 and not args.no_rising and args.precision == "fp32" and args.workload == "roofline":
         rising = rising_bubble_form(args, stream)
@@ -513,7 +551,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
             "gpu_launches": args.steps, "precision_forms": forms, "batched_form": batched,
-            "rising_bubble": rising,
+            "rising_bubble": rising, "unfused_form": unfused,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -65,6 +65,24 @@ typedef enum {
  * and the hydrodynamic p* are kept to FP32 rounding. */
 enum { LBM_PRECISION_FP32 = 0, LBM_PRECISION_FP16 = 1, LBM_PRECISION_BF16 = 2 };
 
+/* Phase-field collision.  SRT: Omega = omega_phi I (Section 5's D3Q15 SRT, the
+ * benchmarked form).  MRT: Omega = M^-1 S M of Section 3.1 with the first-order
+ * moments relaxed by omega_phi and all other moments by 1, in a moment basis
+ * orthogonal under the lattice weights; computed in closed form as
+ * h*_i = h^eq_i + F_i/2 + (1 - omega_phi) w_i e_i . J / c_s^2 with
+ * J = sum_j e_j (h_j - h^eq_j + F_j/2).  MRT needs FP32 storage and a single
+ * simulation (not a batch member). */
+enum { LBM_PHASE_SRT = 0, LBM_PHASE_MRT = 1 };
+
+/* Kernel form of a time step.  FUSED: one kernel per step (Algorithm 2 with the
+ * hydro(k-1) + phase(k) bracketing, in-place AA streaming, one copy of each
+ * lattice: 344 B moved per cell at D3Q27).  UNFUSED: the passes of the paper's
+ * straightforward Algorithm 1 -- a collision kernel for each lattice (storing u
+ * and phi) and a streaming kernel for each, over two grids (708 B per cell at
+ * D3Q27) -- computing the same update; the baseline the fused form is measured
+ * against (Section 4.2).  UNFUSED needs FP32 storage and a single simulation. */
+enum { LBM_FORM_FUSED = 0, LBM_FORM_UNFUSED = 1 };
+
 /* Box and lattices (Section 3; Section 5 uses D3Q15 for h and D3Q27 for g). */
 typedef struct {
     int nx, ny, nz; /* cells per axis, each >= 1, nx*ny*nz < 2^31,
@@ -93,6 +111,8 @@ typedef struct {
                              heavy fluid, 0 mostly light); ignored for FP32          */
     double store_g_scale; /* 16-bit storage: power of two scaling g into the format's
                              normal range; 0 selects 4096 (FP16) or 1 (BF16)        */
+    int phase_collision;  /* LBM_PHASE_SRT or LBM_PHASE_MRT                          */
+    int kernel_form;      /* LBM_FORM_FUSED or LBM_FORM_UNFUSED                      */
 } lbm_params;
 
 /* Diagnostics returned by lbm_reduce (FP64 accumulation).  "Light" weights a
@@ -117,7 +137,8 @@ enum {
 };
 
 /* Bytes of device workspace lbm_create needs for this problem (populations h
- * and g, two phi buffers, flags and reduction scratch).  Host-only; never
+ * and g, two phi buffers, flags and reduction scratch; the unfused form adds a
+ * second grid of both lattices and the velocity field).  Host-only; never
  * touches the GPU. */
 lbm_status lbm_workspace_size(const lbm_domain *dom, const lbm_params *prm, size_t *bytes);
 
@@ -196,8 +217,9 @@ typedef struct lbm_batch_t lbm_batch_t; /* opaque batch handle */
 lbm_status lbm_batch_workspace_size(int count, const lbm_domain *doms, const lbm_params *prms, size_t *bytes);
 
 /* Creates a batch of count (1..65536) members from count domains and
- * parameter sets (validated as by lbm_create; every q_hydro equal and every
- * precision LBM_PRECISION_FP32, else LBM_ERR_ARG) on the current CUDA device.
+ * parameter sets (validated as by lbm_create; every q_hydro equal, every
+ * precision LBM_PRECISION_FP32, every phase_collision LBM_PHASE_SRT and every
+ * kernel_form LBM_FORM_FUSED, else LBM_ERR_ARG) on the current CUDA device.
  * cuda_stream: stream for all of the batch's work (members included), NULL for
  * the legacy default stream (then no CUDA graphs are used).  workspace: device
  * buffer of lbm_batch_workspace_size() bytes, 256-byte aligned, owned by the

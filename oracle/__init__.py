@@ -60,6 +60,7 @@ class orc_problem(ctypes.Structure):
         ("rho_ref", ctypes.c_double),
         ("theta_from_local_phi", ctypes.c_int),
         ("clamp_phi", ctypes.c_int),
+        ("phase_mrt", ctypes.c_int),
     ]
 
 
@@ -116,7 +117,7 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def make_problem(prob, theta_from_local_phi: bool = False, clamp_phi=None) -> orc_problem:
+def make_problem(prob, theta_from_local_phi: bool = False, clamp_phi=None, phase_mrt=None) -> orc_problem:
     """Builds the C problem record from a ``workloads.Problem``-like object."""
     p = orc_problem()
     p.nx, p.ny, p.nz = int(prob.nx), int(prob.ny), int(prob.nz)
@@ -130,6 +131,7 @@ def make_problem(prob, theta_from_local_phi: bool = False, clamp_phi=None) -> or
     p.rho_ref = float(prob.rho_ref)
     p.theta_from_local_phi = int(theta_from_local_phi)
     p.clamp_phi = int(getattr(prob, "clamp_phi", 0) if clamp_phi is None else clamp_phi)
+    p.phase_mrt = int(getattr(prob, "phase_mrt", 0) if phase_mrt is None else phase_mrt)
     return p
 
 

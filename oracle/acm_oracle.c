@@ -139,6 +139,10 @@ typedef struct {
     double rho_ref;   /* buoyancy reference density: F_b = (rho - rho_ref) g  */
     int theta_from_local_phi; /* reading flag, default 0                      */
     int clamp_phi;            /* reading flag, default 0                      */
+    int phase_mrt;            /* 0: SRT phase collision (Section 5's D3Q15 SRT);
+                                 1: MRT of Section 3.1 -- first-order moments
+                                 relaxed with omega_phi, all others with 1, in a
+                                 weighted-orthogonal moment basis              */
 } orc_problem;
 
 typedef struct {
@@ -277,16 +281,35 @@ void orc_phase_cell(const orc_problem *P, const double *h, const double *nbprev,
     double theta = (1.0 - 4.0 * (phi_theta - phi0) * (phi_theta - phi0)) / P->xi;
 
     double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double heq[15], F[15];
     for (int i = 0; i < 15; ++i) {
         double eu = L.e[i][0] * u[0] + L.e[i][1] * u[1] + L.e[i][2] * u[2];
         double en = L.e[i][0] * n[0] + L.e[i][1] * n[1] + L.e[i][2] * n[2];
         /* Gamma_i (Section 3.1) and h^eq = phi Gamma_i */
         double Gamma = L.w[i] * (1.0 + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
-        double heq = phi * Gamma;
+        heq[i] = phi * Gamma;
         /* eq:interfaceTracking */
-        double F = theta * L.w[i] * en;
+        F[i] = theta * L.w[i] * en;
+    }
+    if (!P->phase_mrt) {
         /* eq:lb_interface with Omega = omega_phi * identity */
-        hstar[i] = h[i] + d.omega_phi * (heq - h[i] - 0.5 * F) + F;
+        for (int i = 0; i < 15; ++i) hstar[i] = h[i] + d.omega_phi * (heq[i] - h[i] - 0.5 * F[i]) + F[i];
+    } else {
+        /* eq:lb_interface with Omega = M^-1 S M.  In a moment basis orthogonal
+         * under the weights w (sum_i w_i M_ki M_li = 0 for k != l), the part of a
+         * vector y in the first-order moments is w_i e_i . (sum_j e_j y_j) / c_s^2;
+         * S relaxes those with omega_phi and every other moment with 1, so
+         * Omega y = y - (1 - omega_phi) w_i e_i . (sum_j e_j y_j) / c_s^2. */
+        double y[15], J[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < 15; ++i) {
+            y[i] = heq[i] - h[i] - 0.5 * F[i];
+            for (int a = 0; a < 3; ++a) J[a] += L.e[i][a] * y[i];
+        }
+        for (int i = 0; i < 15; ++i) {
+            double eJ = L.e[i][0] * J[0] + L.e[i][1] * J[1] + L.e[i][2] * J[2];
+            double Oy = y[i] - (1.0 - d.omega_phi) * L.w[i] * eJ / CS2;
+            hstar[i] = h[i] + Oy + F[i];
+        }
     }
     *phi_out = phi;
 }

@@ -21,7 +21,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIBRARY = os.path.join(LIBDIR, "liblbm.so")
 
-SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_aux.cu", "lbm_noalloc.cu", "lbm_batch.cu"]
+SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_aux.cu", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_unfused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-I", CSRC, "-I", INCLUDE]

@@ -17,7 +17,7 @@ namespace {
 thread_local std::string g_create_error;
 
 struct Layout {
-    size_t h_rest, h_mov, g_rest, g_mov, phi0, phi1, flag, red_scratch, red_out, total;
+    size_t h_rest, h_mov, g_rest, g_mov, phi0, phi1, flag, red_scratch, red_out, h_tmp, g_tmp, u, total;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -25,7 +25,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 size_t storage_bytes(int precision) { return precision == LBM_PRECISION_FP32 ? 4 : 2; }
 
 // rest plane (FP32) then the moving planes in the storage type, for h and g
-Layout layout(const lbm_domain &d, int precision) {
+Layout layout(const lbm_domain &d, int precision, int form) {
     const size_t N = (size_t)d.nx * d.ny * d.nz, b = storage_bytes(precision);
     Layout L;
     size_t off = 0;
@@ -47,6 +47,15 @@ Layout layout(const lbm_domain &d, int precision) {
     off = align256(off + (size_t)lbm::kReduceBlocks * lbm::kDiagSlots * sizeof(double));
     L.red_out = off;
     off = align256(off + lbm::kDiagSlots * sizeof(double));
+    L.h_tmp = L.g_tmp = L.u = 0;
+    if (form == LBM_FORM_UNFUSED) {  // second grid of both lattices, stored velocity
+        L.h_tmp = off;
+        off = align256(off + 15 * N * sizeof(float));
+        L.g_tmp = off;
+        off = align256(off + (size_t)d.q_hydro * N * sizeof(float));
+        L.u = off;
+        off = align256(off + 3 * N * sizeof(float));
+    }
     L.total = off;
     return L;
 }
@@ -82,6 +91,14 @@ lbm_status validate(const lbm_domain *d, const lbm_params *p, std::string &why) 
         if (m != 0.5 || ex < -40 || ex > 40) return why = "store_g_scale must be 0 or a power of two", LBM_ERR_ARG;
     }
     if (p->clamp_phi != 0 && p->clamp_phi != 1) return why = "clamp_phi must be 0 or 1", LBM_ERR_ARG;
+    if (p->phase_collision != LBM_PHASE_SRT && p->phase_collision != LBM_PHASE_MRT)
+        return why = "phase_collision must be LBM_PHASE_SRT or LBM_PHASE_MRT", LBM_ERR_ARG;
+    if (p->phase_collision == LBM_PHASE_MRT && p->precision != LBM_PRECISION_FP32)
+        return why = "the MRT phase collision is built for FP32 storage", LBM_ERR_ARG;
+    if (p->kernel_form != LBM_FORM_FUSED && p->kernel_form != LBM_FORM_UNFUSED)
+        return why = "kernel_form must be LBM_FORM_FUSED or LBM_FORM_UNFUSED", LBM_ERR_ARG;
+    if (p->kernel_form == LBM_FORM_UNFUSED && p->precision != LBM_PRECISION_FP32)
+        return why = "the unfused form is built for FP32 storage", LBM_ERR_ARG;
     const double rho_L = p->rho_H / p->rho_ratio;
     const double nu_L = p->nu_H * p->rho_H / (p->mu_ratio * rho_L);
     if (!(rho_L > 0) || !finite(rho_L)) return why = "rho_L = rho_H / rho_ratio must be positive", LBM_ERR_ARG;
@@ -116,6 +133,7 @@ lbm::Params derive(const lbm_domain &d, const lbm_params &p) {
     k.rho_ref = (float)p.rho_ref;
     k.phi_lo = p.clamp_phi ? 0.0f : -INFINITY;
     k.phi_hi = p.clamp_phi ? 1.0f : INFINITY;
+    k.phase_mrt = p.phase_collision == LBM_PHASE_MRT ? 1 : 0;
     if (p.precision == LBM_PRECISION_FP32) {
         k.h_ref = 0.0f;
         k.g_scale = k.g_inv_scale = 1.0f;
@@ -150,8 +168,10 @@ lbm_status cuda_fail(lbm_t *s, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(s, e_, #call); \
     } while (0)
 
-bool g_swapped(const lbm_t *s) { return (s->t & 1) != 0; }
-bool h_swapped(const lbm_t *s) { return ((s->t + 1) & 1) != 0; }
+// In-place AA layout of each lattice at the current level (the unfused form
+// keeps both natural).
+bool g_swapped(const lbm_t *s) { return !s->unfused && (s->t & 1) != 0; }
+bool h_swapped(const lbm_t *s) { return !s->unfused && ((s->t + 1) & 1) != 0; }
 size_t plane_bytes(const lbm_t *s) { return (size_t)s->kp.N * sizeof(float); }
 
 cudaMemcpyKind kind_to_device(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
@@ -185,7 +205,7 @@ lbm_status lbm_workspace_size(const lbm_domain *dom, const lbm_params *prm, size
         g_create_error = why;
         return st;
     }
-    *bytes = layout(*dom, prm->precision).total;
+    *bytes = layout(*dom, prm->precision, prm->kernel_form).total;
     return LBM_OK;
 }
 
@@ -196,7 +216,7 @@ lbm_status lbm_create(lbm_t **out, const lbm_domain *dom, const lbm_params *prm,
     std::string why;
     lbm_status st = validate(dom, prm, why);
     if (st != LBM_OK) return g_create_error = why, st;
-    const Layout L = layout(*dom, prm->precision);
+    const Layout L = layout(*dom, prm->precision, prm->kernel_form);
     if (workspace) {
         if (workspace_bytes < L.total) return g_create_error = "workspace smaller than lbm_workspace_size()", LBM_ERR_OOM;
         if (((uintptr_t)workspace & 255) != 0) return g_create_error = "workspace must be 256-byte aligned", LBM_ERR_ARG;
@@ -238,6 +258,10 @@ lbm_status lbm_create(lbm_t **out, const lbm_domain *dom, const lbm_params *prm,
     s->flag = (int *)(s->ws + L.flag);
     s->red_scratch = (double *)(s->ws + L.red_scratch);
     s->red_out = (double *)(s->ws + L.red_out);
+    s->unfused = prm->kernel_form == LBM_FORM_UNFUSED;
+    s->uf.h_tmp = s->unfused ? (float *)(s->ws + L.h_tmp) : nullptr;
+    s->uf.g_tmp = s->unfused ? (float *)(s->ws + L.g_tmp) : nullptr;
+    s->uf.u = s->unfused ? (float *)(s->ws + L.u) : nullptr;
     s->cur = 0;
     s->t = 0;
     s->ready = false;
@@ -260,8 +284,14 @@ lbm_status lbm_init_phase(lbm_t *s, const float *phi0, int phi0_on_device) {
     LBM_CK(s, lbm::launch_init(s->kp, s->sto, s->dom.q_hydro, s->phi[0], s->stream));
     LBM_CK(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
     // time level 0: the first phase-field step alone (u_{-1} = 0, phi^{-1} = phi0)
-    LBM_CK(s, lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, false, false, false, s->phi[0], s->phi[1], s->flag,
-                               s->stream));
+    if (s->unfused) {
+        LBM_CK(s, cudaMemsetAsync(s->uf.u, 0, 3 * plane_bytes(s), s->stream));
+        LBM_CK(s, lbm::launch_unfused(s->kp, s->uf, s->sto, s->dom.q_hydro, false, s->phi[0], s->phi[1], s->flag,
+                                      s->stream));
+    } else {
+        LBM_CK(s, lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, false, false, false, s->phi[0], s->phi[1],
+                                   s->flag, s->stream));
+    }
     s->cur = 1;
     s->t = 0;
     s->ready = true;
@@ -273,8 +303,12 @@ lbm_status lbm_step(lbm_t *s, int64_t n) {
     if (!s->ready) return s->err = "lbm_step before lbm_init_phase / lbm_set_state", LBM_ERR_STATE;
     DeviceGuard dg(s->device);
     for (int64_t k = 0; k < n; ++k) {
-        LBM_CK(s, lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, g_swapped(s), h_swapped(s), true, s->phi[s->cur],
-                                   s->phi[s->cur ^ 1], s->flag, s->stream));
+        if (s->unfused)
+            LBM_CK(s, lbm::launch_unfused(s->kp, s->uf, s->sto, s->dom.q_hydro, true, s->phi[s->cur],
+                                          s->phi[s->cur ^ 1], s->flag, s->stream));
+        else
+            LBM_CK(s, lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, g_swapped(s), h_swapped(s), true,
+                                       s->phi[s->cur], s->phi[s->cur ^ 1], s->flag, s->stream));
         s->cur ^= 1;
         s->t += 1;
     }

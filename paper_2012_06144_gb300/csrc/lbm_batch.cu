@@ -31,7 +31,7 @@
 
 namespace lbm {
 
-constexpr int kGroup = 64;  // members per launch: 64 descriptors of 488 bytes fit the 32 KB parameter block
+constexpr int kGroup = 64;  // members per launch: 64 descriptors fit the 32 KB parameter block
 constexpr int kGraphSteps = 16;
 
 struct MemberDesc {
@@ -60,9 +60,9 @@ __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
     __shared__ float tile[TZ + 2][TY + 2][TX + 2];
     const int4 e = tiles[blockIdx.x];
     const MemberDesc &d = a.m[e.x];
-    tile_update<float, QG, G_SW, H_SW, true, TY, TZ>(d.p, TableLat{d.pl.h}, TableLat{d.pl.g}, d.phi[cur],
-                                                     d.phi[cur ^ 1], d.flag, tile, e.y, e.z, e.w, threadIdx.x,
-                                                     threadIdx.y, threadIdx.z);
+    tile_update<float, QG, G_SW, H_SW, true, false, TY, TZ>(d.p, TableLat{d.pl.h}, TableLat{d.pl.g}, d.phi[cur],
+                                                            d.phi[cur ^ 1], d.flag, tile, e.y, e.z, e.w,
+                                                            threadIdx.x, threadIdx.y, threadIdx.z);
 }
 
 template <int QG, bool G_SW, bool H_SW, int TY, int TZ>
@@ -277,6 +277,10 @@ lbm_status lbm_batch_create(lbm_batch_t **out, int count, const lbm_domain *doms
             return lbm::set_thread_error("all members need the same hydrodynamic lattice"), LBM_ERR_ARG;
         if (prms[i].precision != LBM_PRECISION_FP32)
             return lbm::set_thread_error("batched stepping supports FP32 storage only"), LBM_ERR_ARG;
+        if (prms[i].phase_collision != LBM_PHASE_SRT)
+            return lbm::set_thread_error("batched stepping supports the SRT phase collision only"), LBM_ERR_ARG;
+        if (prms[i].kernel_form != LBM_FORM_FUSED)
+            return lbm::set_thread_error("batched stepping runs the fused form only"), LBM_ERR_ARG;
     }
     if (workspace) {
         size_t need = 0;

@@ -115,6 +115,7 @@ struct Params {
     // reduced-precision storage of the moving populations (ignored for FP32):
     // h_i stored as h_i - w_i h_ref, g_i stored as g_i * g_scale
     float h_ref, g_scale, g_inv_scale;
+    int phase_mrt;  // 1: MRT phase collision (selects the kernel instance on the host)
 };
 
 // One lattice as seen by the auxiliary kernels: slot 0 (rest) in FP32, slot s >= 1

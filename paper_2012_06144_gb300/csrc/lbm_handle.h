@@ -18,6 +18,8 @@ struct lbm_t {
     size_t ws_bytes;
     bool owns_ws;
     lbm::Storage sto;
+    bool unfused;      // LBM_FORM_UNFUSED: natural two-grid storage, Algorithm 1's passes
+    lbm::Unfused uf;
     float *phi[2];
     int *flag;
     double *red_scratch, *red_out;

@@ -22,6 +22,17 @@ struct Storage {
     LatticeMem h, g;
 };
 
+// Extra buffers of the unfused baseline (FP32, natural layout): post-collision
+// populations of both lattices and the stored velocity field (3 planes).
+struct Unfused {
+    float *h_tmp, *g_tmp, *u;
+};
+
+// One time step of the unfused baseline: hydro collision (if hydro), phase
+// collision, streaming of h, streaming of g (if hydro), over two grids.
+cudaError_t launch_unfused(const Params &p, const Unfused &uf, const Storage &sto, int q_hydro, bool hydro,
+                           const float *phi_in, float *phi_out, int *flag, cudaStream_t st);
+
 // One launch of the fused kernel K_k = hydro(k-1) + phase(k) (hydro = true), or
 // the first phase step alone (hydro = false).  g_swapped / h_swapped give the
 // current AA layout of each lattice.

@@ -30,21 +30,21 @@ namespace lbm {
 
 constexpr int TY = LBM_TY, TZ = LBM_TZ;
 
-template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO>
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool PMRT>
 __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
     fused_step_kernel(Params p, Planes pl, const float *__restrict__ phi_in, float *__restrict__ phi_out,
                       int *__restrict__ flag) {
     __shared__ float tile[TZ + 2][TY + 2][TX + 2];
-    tile_update<T, QG, G_SW, H_SW, HYDRO, TY, TZ>(p, TableLat{pl.h}, TableLat{pl.g}, phi_in, phi_out, flag, tile,
-                                                  blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x,
-                                                  threadIdx.y, threadIdx.z);
+    tile_update<T, QG, G_SW, H_SW, HYDRO, PMRT, TY, TZ>(p, TableLat{pl.h}, TableLat{pl.g}, phi_in, phi_out, flag,
+                                                        tile, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x,
+                                                        threadIdx.y, threadIdx.z);
 }
-template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO>
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool PMRT = false>
 static cudaError_t launch(const Params &p, const Planes &pl, const float *pi, float *po, int *flag,
                           cudaStream_t st) {
     const dim3 block(TX, TY, TZ);
     const dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + TZ - 1) / TZ);
-    fused_step_kernel<T, QG, G_SW, H_SW, HYDRO><<<grid, block, 0, st>>>(p, pl, pi, po, flag);
+    fused_step_kernel<T, QG, G_SW, H_SW, HYDRO, PMRT><<<grid, block, 0, st>>>(p, pl, pi, po, flag);
     return cudaGetLastError();
 }
 
@@ -70,8 +70,35 @@ static cudaError_t launch_typed(const Params &p, const Storage &sto, int q_hydro
     return cudaErrorInvalidValue;
 }
 
+// The MRT phase collision (FP32 storage only).
+static cudaError_t launch_mrt(const Params &p, const Storage &sto, int q_hydro, bool g_sw, bool h_sw, bool hydro,
+                              const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
+    Planes pl;
+    pl.h[0] = sto.h.rest;
+    for (int i = 1; i < 15; ++i) pl.h[i] = static_cast<float *>(sto.h.mov) + (size_t)(i - 1) * p.N;
+    pl.g[0] = sto.g.rest;
+    for (int i = 1; i < 27; ++i)
+        pl.g[i] = i < q_hydro ? static_cast<float *>(sto.g.mov) + (size_t)(i - 1) * p.N : nullptr;
+    if (!hydro) {
+        if (h_sw) return cudaErrorInvalidValue;
+        return launch<float, 19, false, false, false, true>(p, pl, phi_in, phi_out, flag, st);
+    }
+    if (g_sw == h_sw) return cudaErrorInvalidValue;
+    if (q_hydro == 19)
+        return g_sw ? launch<float, 19, true, false, true, true>(p, pl, phi_in, phi_out, flag, st)
+                    : launch<float, 19, false, true, true, true>(p, pl, phi_in, phi_out, flag, st);
+    if (q_hydro == 27)
+        return g_sw ? launch<float, 27, true, false, true, true>(p, pl, phi_in, phi_out, flag, st)
+                    : launch<float, 27, false, true, true, true>(p, pl, phi_in, phi_out, flag, st);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_step(const Params &p, const Storage &sto, int q_hydro, bool g_sw, bool h_sw, bool hydro,
                         const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
+    if (p.phase_mrt) {
+        if (sto.precision != LBM_PRECISION_FP32) return cudaErrorInvalidValue;
+        return launch_mrt(p, sto, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
+    }
     switch (sto.precision) {
         case LBM_PRECISION_FP32:
             return launch_typed<float>(p, sto, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);

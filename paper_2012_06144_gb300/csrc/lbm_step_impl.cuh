@@ -167,7 +167,7 @@ __device__ __forceinline__ void pop_store_enc(const L &lat, const Nb3 &n, int i,
 // Collision of both lattices at one cell and the streaming stores, from the
 // pre-collision populations gv (g^{k-1}), hv (h^k) and the 3x3x3 neighbourhood nb
 // of phi^{k-1}.
-template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE, typename LH, typename LG>
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, bool EDGE, typename LH, typename LG>
 __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh, const LG &lg, const Nb3 &n, const float *gv,
                                                   const float *hv, const float *nb, float *__restrict__ phi_out,
                                                   int *__restrict__ flag) {
@@ -227,7 +227,29 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh,
     const float pc = phic - 0.5f;
     const float theta = (1.0f - 4.0f * pc * pc) * p.inv_xi;
     const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
-    const float om = p.omega_phi, fc = 1.0f - 0.5f * om;
+    float om = p.omega_phi, fc = 1.0f - 0.5f * om;
+    // MRT (Section 3.1, first-order moments relaxed with omega_phi, the rest with
+    // 1, weighted-orthogonal basis): the SRT update with rate 1 plus
+    // (1 - omega_phi) w_i e_i . J / c_s^2, J = sum_j e_j (h_j - h^eq_j + F_j / 2)
+    //   = sum_j e_j h_j - phi_k u + theta c_s^2 n / 2.
+    float cJx = 0.f, cJy = 0.f, cJz = 0.f;
+    if constexpr (PMRT) {
+        float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+        for (int i = 1; i < 15; i += 2) {
+            const V3 e = vel<15>(i);
+            const float dh = hv[i] - hv[i + 1];
+            jx += e.x * dh;
+            jy += e.y * dh;
+            jz += e.z * dh;
+        }
+        const float c = 3.0f * (1.0f - om), th = theta * (0.5f / 3.0f);
+        cJx = c * (fmaf(th, nx, jx) - phik * ux);
+        cJy = c * (fmaf(th, ny, jy) - phik * uy);
+        cJz = c * (fmaf(th, nz, jz) - phik * uz);
+        om = 1.0f;
+        fc = 0.5f;
+    }
     // h*_i = h_i + omega (h^eq_i - h_i - F_i/2) + F_i over opposite pairs, with
     // h^eq = phi_k w (1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u) and F_i = theta w e.n.
     // The non-equilibrium h^eq_i - h_i is formed as fma(phi_k, w, -h_i) + phi_k w
@@ -249,8 +271,13 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh,
         const float F = fc * (theta * w * en);
         const float neq_a = fmaf(phik, w, -hv[i]) + (x_even + x_odd);
         const float neq_b = fmaf(phik, w, -hv[i + 1]) + (x_even - x_odd);
-        const float a = hv[i] + fmaf(om, neq_a, F);
-        const float b = hv[i + 1] + fmaf(om, neq_b, -F);
+        float a = hv[i] + fmaf(om, neq_a, F);
+        float b = hv[i + 1] + fmaf(om, neq_b, -F);
+        if constexpr (PMRT) {
+            const float corr = w * (e.x * cJx + e.y * cJy + e.z * cJz);
+            a += corr;
+            b -= corr;
+        }
         const T qa = ch.template encode<15>(a, i), qb = ch.template encode<15>(b, i + 1);
         pop_store_enc<T, 15, H_SW, EDGE>(lh, n, i, qa);
         pop_store_enc<T, 15, H_SW, EDGE>(lh, n, i + 1, qb);
@@ -259,7 +286,8 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh,
     pop_store_rest<T, 15, H_SW, EDGE>(lh, n, hv[0] - dsum);
 }
 
-template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool EDGE, int TY, int TZ, typename LH, typename LG>
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, bool EDGE, int TY, int TZ, typename LH,
+          typename LG>
 __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const LG &lg, const Nb3 &n, bool active,
                                             const float *__restrict__ phi_in, float (*tile)[TY + 2][TX + 2],
                                             float *__restrict__ phi_out, int *__restrict__ flag, int bx, int by,
@@ -322,13 +350,13 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx)
                 nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
-    collide_and_store<T, QG, G_SW, H_SW, HYDRO, EDGE>(p, lh, lg, n, gv, hv, nb, phi_out, flag);
+    collide_and_store<T, QG, G_SW, H_SW, HYDRO, PMRT, EDGE>(p, lh, lg, n, gv, hv, nb, phi_out, flag);
 }
 
 // One tile (bx, by, bz) of 32 x TY x TZ cells, one thread per cell: per-thread
 // neighbour offsets, then the bounce-back-checking path only if the tile touches
 // a walled face.  Every thread of the block must call this (it synchronises).
-template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, int TY, int TZ, typename LH, typename LG>
+template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, int TY, int TZ, typename LH, typename LG>
 __device__ __forceinline__ void tile_update(const Params &p, const LH &lh, const LG &lg,
                                             const float *__restrict__ phi_in, float *__restrict__ phi_out,
                                             int *__restrict__ flag, float (*tile)[TY + 2][TX + 2], int bx, int by,
@@ -358,10 +386,10 @@ __device__ __forceinline__ void tile_update(const Params &p, const LH &lh, const
     const bool edge = (wx && (bx == 0 || (bx + 1) * TX >= p.nx)) || (wy && (by == 0 || (by + 1) * TY >= p.ny)) ||
                       (wz && (bz == 0 || (bz + 1) * TZ >= p.nz));
     if (edge)
-        cell_update<T, QG, G_SW, H_SW, HYDRO, true, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+        cell_update<T, QG, G_SW, H_SW, HYDRO, PMRT, true, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
                                                             by, bz, tx, ty, tz);
     else
-        cell_update<T, QG, G_SW, H_SW, HYDRO, false, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+        cell_update<T, QG, G_SW, H_SW, HYDRO, PMRT, false, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
                                                              by, bz, tx, ty, tz);
 }
 

@@ -21,6 +21,8 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_STATE 
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM", -4: "LBM_ERR_DIVERGED",
                 -5: "LBM_ERR_STATE"}
 LBM_PRECISION_FP32, LBM_PRECISION_FP16, LBM_PRECISION_BF16 = 0, 1, 2
+LBM_PHASE_SRT, LBM_PHASE_MRT = 0, 1
+LBM_FORM_FUSED, LBM_FORM_UNFUSED = 0, 1
 PRECISIONS = {"fp32": LBM_PRECISION_FP32, "fp16": LBM_PRECISION_FP16, "bf16": LBM_PRECISION_BF16}
 DIAG_NAMES = ["mass", "mom_x", "mom_y", "mom_z", "light_vol", "light_x", "light_y", "light_z", "light_ux",
               "light_uy", "light_uz", "max_u"]
@@ -37,7 +39,8 @@ class lbm_params(ctypes.Structure):
                 ("mu_ratio", ctypes.c_double), ("sigma", ctypes.c_double), ("xi", ctypes.c_double),
                 ("mobility", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("rho_ref", ctypes.c_double),
                 ("precision", ctypes.c_int), ("clamp_phi", ctypes.c_int), ("store_phi_ref", ctypes.c_double),
-                ("store_g_scale", ctypes.c_double)]
+                ("store_g_scale", ctypes.c_double), ("phase_collision", ctypes.c_int),
+                ("kernel_form", ctypes.c_int)]
 
 
 class LBMError(RuntimeError):
@@ -133,7 +136,7 @@ def make_domain(nx, ny, nz, wall=(0, 0, 0), q_hydro=27, q_phase=15) -> lbm_domai
 
 def make_params(rho_H=1.0, rho_ratio=1000.0, nu_H=0.01, mu_ratio=100.0, sigma=1e-4, xi=5.0, mobility=0.02,
                 gravity=(0.0, 0.0, 0.0), rho_ref=0.0, precision=LBM_PRECISION_FP32, clamp_phi=0, store_phi_ref=0.0,
-                store_g_scale=0.0) -> lbm_params:
+                store_g_scale=0.0, phase_collision=LBM_PHASE_SRT, kernel_form=LBM_FORM_FUSED) -> lbm_params:
     p = lbm_params()
     p.rho_H, p.rho_ratio, p.nu_H, p.mu_ratio = float(rho_H), float(rho_ratio), float(nu_H), float(mu_ratio)
     p.sigma, p.xi, p.mobility = float(sigma), float(xi), float(mobility)
@@ -141,6 +144,8 @@ def make_params(rho_H=1.0, rho_ratio=1000.0, nu_H=0.01, mu_ratio=100.0, sigma=1e
         p.gravity[a] = float(gravity[a])
     p.rho_ref, p.precision, p.clamp_phi = float(rho_ref), int(precision), int(clamp_phi)
     p.store_phi_ref, p.store_g_scale = float(store_phi_ref), float(store_g_scale)
+    p.phase_collision = int(phase_collision)
+    p.kernel_form = int(kernel_form)
     return p
 
 
@@ -152,7 +157,9 @@ def from_problem(prob, precision=None):
     prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     p = make_params(prob.rho_H, prob.rho_ratio, prob.nu_H, prob.mu_ratio, prob.sigma, prob.xi, prob.mobility,
                     prob.gravity, prob.rho_ref, precision=prec, clamp_phi=int(getattr(prob, "clamp_phi", 0)),
-                    store_phi_ref=float(getattr(prob, "store_phi_ref", 0.0)))
+                    store_phi_ref=float(getattr(prob, "store_phi_ref", 0.0)),
+                    phase_collision=LBM_PHASE_MRT if getattr(prob, "phase_mrt", 0) else LBM_PHASE_SRT,
+                    kernel_form=LBM_FORM_UNFUSED if getattr(prob, "unfused", 0) else LBM_FORM_FUSED)
     return d, p
 
 

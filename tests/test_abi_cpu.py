@@ -95,6 +95,7 @@ def test_invalid_domain_rejected(lbm, field, value):
     ("rho_H", 0.0), ("rho_ratio", -1.0), ("nu_H", 0.0), ("mu_ratio", 0.0), ("sigma", -1e-4), ("xi", 0.0),
     ("mobility", 0.0), ("rho_ref", float("nan")), ("precision", 7), ("nu_H", float("inf")),
     ("store_g_scale", 3.0), ("store_g_scale", -4.0), ("store_phi_ref", float("inf")), ("clamp_phi", 2),
+    ("phase_collision", 2), ("phase_collision", -1), ("kernel_form", 2),
 ])
 def test_invalid_params_rejected(lbm, field, value):
     p = lbm.make_params()
@@ -183,3 +184,30 @@ def test_batch_null_handle_calls(lbm):
     assert lib.lbm_batch_member(None, 0) is None
     assert lib.lbm_batch_last_error(None) == b""
     lib.lbm_batch_destroy(None)
+
+
+def test_mrt_phase_needs_fp32_storage(lbm):
+    d = lbm.make_domain(8, 8, 8)
+    for prec in (lbm.LBM_PRECISION_FP16, lbm.LBM_PRECISION_BF16):
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_workspace_size(d, lbm.make_params(precision=prec, phase_collision=lbm.LBM_PHASE_MRT))
+        assert ei.value.status == lbm.LBM_ERR_ARG
+    assert lbm.lbm_workspace_size(d, lbm.make_params(phase_collision=lbm.LBM_PHASE_MRT)) > 0
+    with pytest.raises(lbm.LBMError) as ei:  # batches take the SRT phase collision only
+        lbm.lbm_batch_create([d, d], [lbm.make_params(), lbm.make_params(phase_collision=lbm.LBM_PHASE_MRT)])
+    assert ei.value.status == lbm.LBM_ERR_ARG
+
+
+def test_unfused_form_workspace_and_limits(lbm):
+    d = lbm.make_domain(16, 8, 4, q_hydro=27)
+    fused = lbm.lbm_workspace_size(d, lbm.make_params())
+    unfused = lbm.lbm_workspace_size(d, lbm.make_params(kernel_form=lbm.LBM_FORM_UNFUSED))
+    N = 16 * 8 * 4
+    assert unfused >= fused + (15 + 27 + 3) * N * 4  # second grid of both lattices and the velocity field
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_workspace_size(d, lbm.make_params(precision=lbm.LBM_PRECISION_FP16,
+                                                  kernel_form=lbm.LBM_FORM_UNFUSED))
+    assert ei.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_batch_create([d, d], [lbm.make_params(), lbm.make_params(kernel_form=lbm.LBM_FORM_UNFUSED)])
+    assert ei.value.status == lbm.LBM_ERR_ARG

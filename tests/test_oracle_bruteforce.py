@@ -146,3 +146,54 @@ def test_moment_matrix_is_weighted_orthogonal(orc):
         N = M @ np.diag(w) @ M.T
         assert np.abs(N - np.diag(np.diag(N))).max() < 1e-12
         assert list(deg[:10]) == [0, 1, 1, 1, 2, 2, 2, 2, 2, 2]
+
+
+def literal_phase_mrt_step(prob, orc, h, phi_prev, u_prev):
+    """eq:lb_interface with Omega = M^{-1} S M literally (Section 3.1): M the
+    w-orthogonal D3Q15 moment matrix, S relaxing the first-order moments with
+    omega_phi and every other moment with 1."""
+    e15, w15, _ = orc.lattice(15)
+    omega = 1.0 / (prob.mobility / CS2 + 0.5)
+    M, deg = moment_matrix(e15, w15)
+    Omega = np.linalg.inv(M) @ np.diag(np.where(deg == 1, omega, 1.0)) @ M
+    phi = h.sum(0)
+    G = sum(e15[i][:, None, None, None] * w15[i] * shifted(phi_prev, e15[i]) for i in range(15)) / CS2
+    Gn = np.sqrt((G ** 2).sum(0))
+    n = np.where(Gn ** 2 > 1e-24, G / np.where(Gn > 0, Gn, 1), 0.0)
+    theta = (1 - 4 * (phi_prev - 0.5) ** 2) / prob.xi
+    uu = (u_prev ** 2).sum(0)
+    heq, F = np.zeros_like(h), np.zeros_like(h)
+    for i in range(15):
+        eu = np.einsum("a,a...->...", e15[i].astype(float), u_prev)
+        heq[i] = phi * w15[i] * (1 + eu / CS2 + eu ** 2 / (2 * CS2 ** 2) - uu / (2 * CS2))
+        F[i] = theta * w15[i] * np.einsum("a,a...->...", e15[i].astype(float), n)
+    hs = h + np.einsum("ij,j...->i...", Omega, heq - h - 0.5 * F) + F
+    return np.array([shifted(hs[i], -e15[i]) for i in range(15)]), phi
+
+
+def test_literal_mrt_phase_step(orc):
+    prob = W.Problem(7, 6, 5, wall=(0, 0, 0), q_hydro=27, sigma=2e-3, xi=3.0, mobility=0.07, phase_mrt=1)
+    p = orc.make_problem(prob)
+    rng = np.random.default_rng(12)
+    phi_prev = W.random_smooth_field(prob.shape, rng)
+    h = rng.uniform(0, 0.1, (15,) + prob.shape)
+    u_prev = rng.normal(0, 1e-2, (3,) + prob.shape)
+    h_lit, phi_lit = literal_phase_mrt_step(prob, orc, h, phi_prev, u_prev)
+    h_next, phi_now = orc.phase_step(p, h, phi_prev, u_prev)
+    assert np.abs(phi_now - phi_lit).max() < 1e-14
+    assert np.abs(h_next - h_lit).max() < 1e-14
+    # the MRT step differs from the SRT step (the higher moments relax with 1)
+    h_srt, _ = orc.phase_step(orc.make_problem(prob, phase_mrt=0), h, phi_prev, u_prev)
+    assert np.abs(h_srt - h_lit).max() > 1e-3
+
+
+def test_mrt_phase_with_unit_rate_is_srt(orc):
+    """omega_phi = 1 (M = c_s^2 / 2) relaxes every moment with 1: MRT == SRT."""
+    prob = W.Problem(6, 5, 4, wall=(1, 0, 0), q_hydro=19, sigma=1e-3, xi=3.0, mobility=CS2 / 2)
+    rng = np.random.default_rng(13)
+    phi_prev = W.random_smooth_field(prob.shape, rng)
+    h = rng.uniform(0, 0.1, (15,) + prob.shape)
+    u_prev = rng.normal(0, 1e-2, (3,) + prob.shape)
+    a, _ = orc.phase_step(orc.make_problem(prob, phase_mrt=1), h, phi_prev, u_prev)
+    b, _ = orc.phase_step(orc.make_problem(prob, phase_mrt=0), h, phi_prev, u_prev)
+    assert np.abs(a - b).max() < 1e-15

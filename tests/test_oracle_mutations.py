@@ -3,15 +3,18 @@
 Each entry plants one plausible mistake (a dropped term, a wrong sign, factor,
 index or operand) in a private copy of ``oracle/acm_oracle.c``, compiles it on
 the CPU and runs the closed-form, invariant and physics pins against it.  Every
-mistake must make at least one pin fail.  The brute-force test (which retypes
-the force formulas) and the derived-parameter test are deliberately not in the
-pin list, so that no mutation is caught only by a retyped formula.
+mistake must make at least one pin fail.  The brute-force whole-step test (which
+retypes the force formulas) and the derived-parameter test are deliberately not
+in the pin list, so that no mutation is caught only by a retyped formula; the
+literal moment-matrix MRT phase step is in it (it builds Omega = M^-1 S M from
+the lattice, not from the oracle's closed form).
 """
 import os
 
 import numpy as np
 import pytest
 
+import test_oracle_bruteforce as B
 import test_oracle_identities as I
 import test_oracle_physics as Ph
 
@@ -19,7 +22,7 @@ MUTATIONS = [
     ("gradient without 1/c_s^2", "for (int a = 0; a < 3; ++a) grad[a] /= CS2;", ""),
     ("Laplacian factor 2 dropped", "return 2.0 * s / CS2;", "return s / CS2;"),
     ("theta coefficient", "(1.0 - 4.0 * (phi_theta", "(1.0 - 2.0 * (phi_theta"),
-    ("phase forcing half-step sign", "- 0.5 * F) + F;", "+ 0.5 * F) + F;"),
+    ("phase forcing half-step sign", "- 0.5 * F[i]) + F[i];", "+ 0.5 * F[i]) + F[i];"),
     ("Gamma quadratic coefficient", "eu * eu / (2.0 * CS2 * CS2)", "eu * eu / (CS2 * CS2)"),
     ("phase relaxation literal 1/tau_phi", "d.omega_phi = 1.0 / (tau_phi + 0.5);", "d.omega_phi = 1.0 / tau_phi;"),
     ("normal not normalised", "double inv = 1.0 / sqrt(G2);", "double inv = 1.0;"),
@@ -46,6 +49,11 @@ MUTATIONS = [
     ("wall ghosts wrap instead of mirror", "    if (walled) {", "    if (0) {"),
     ("D3Q15 corner weight", "1.0 / 9.0, 0.0, 1.0 / 72.0}", "1.0 / 9.0, 0.0, 1.0 / 36.0}"),
     ("pressure output without rho", "p[c] = aux[1] * aux[0] * CS2;", "p[c] = aux[1] * CS2;"),
+    ("MRT phase: first-moment rate transposed", "(1.0 - d.omega_phi) * L.w[i] * eJ / CS2",
+     "d.omega_phi * L.w[i] * eJ / CS2"),
+    ("MRT phase: unweighted projection", "(1.0 - d.omega_phi) * L.w[i] * eJ / CS2",
+     "(1.0 - d.omega_phi) * eJ / 10.0"),
+    ("MRT phase: forcing half-step dropped", "y[i] = heq[i] - h[i] - 0.5 * F[i];", "y[i] = heq[i] - h[i];"),
 ]
 
 
@@ -65,7 +73,9 @@ def _pins(orc):
         lambda: I.test_chemical_potential_vanishes_on_equilibrium_profile(orc, 27),
         lambda: I.test_mass_conservation(orc, (1, 1, 1), 27),
         lambda: I.test_trivial_states(orc, 19),
-        lambda: Ph.test_phase_diffusion_rate(orc),
+        lambda: Ph.test_phase_diffusion_rate(orc, 0),
+        lambda: Ph.test_phase_diffusion_rate(orc, 1),
+        lambda: B.test_literal_mrt_phase_step(orc),
         lambda: Ph.test_shear_wave_viscosity(orc, 19),
         lambda: Ph.test_planar_interface_steady(orc, 27),
         lambda: Ph.test_interface_advection(orc),

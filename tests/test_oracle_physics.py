@@ -38,9 +38,14 @@ def _equilibrium_flow(orc, s, prob, u):
     s.u_prev[:] = u
 
 
-def test_phase_diffusion_rate(orc):
+@pytest.mark.parametrize("mrt", [0, 1])
+def test_phase_diffusion_rate(orc, mrt):
+    """A sine mode of phi decays at M k^2 (eq:mobility, reading A2).  The
+    diffusivity is set by the relaxation of the first-order moments alone, so the
+    MRT phase collision (Section 3.1: other moments relaxed with 1) decays at the
+    same rate."""
     prob = W.Problem(64, 1, 1, q_hydro=19, rho_ratio=1.0, mu_ratio=1.0, nu_H=0.1, sigma=0.0, xi=1e9,
-                     mobility=0.05)
+                     mobility=0.05, phase_mrt=mrt)
     p = orc.make_problem(prob)
     x = np.arange(64) + 0.5
     k = 2 * np.pi / 64

@@ -53,6 +53,8 @@ class Problem:
     gravity: tuple = (0.0, 0.0, 0.0)
     rho_ref: float = 1.0
     clamp_phi: int = 0  # 1: phi clamped to [0, 1] inside rho and tau
+    phase_mrt: int = 0  # 1: MRT phase collision of Section 3.1 (0: SRT, the benchmarked form)
+    unfused: int = 0  # 1: run the unfused baseline (Algorithm 1's passes) instead of the fused step
     precision: str = "fp32"  # population storage: "fp32", "fp16", "bf16"
     store_phi_ref: float = 0.0  # 16-bit storage keeps h_i - w_i store_phi_ref (1: mostly heavy fluid)
 
