@@ -15,7 +15,7 @@
 // 15 h + q g + phi and writes 15 h + q g + phi per cell, and no velocity field is
 // stored.  The h lattice runs one time level ahead of g.
 //
-// Layout of the work: a block owns a 32 x 4 x 2 tile of cells (one warp = 32
+// Layout of the work: a block owns a 32 x 2 x 4 tile of cells (one warp = 32
 // consecutive x, so every population plane is read and written in full 128-byte
 // lines).  The warps first issue the row loads of the phi tile with its one-cell
 // halo, then each thread the loads of its 15 + q populations; the tile then goes
@@ -35,15 +35,18 @@ __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
     fused_step_kernel(Params p, Planes pl, const float *__restrict__ phi_in, float *__restrict__ phi_out,
                       int *__restrict__ flag) {
     __shared__ float tile[TZ + 2][TY + 2][TX + 2];
+    // blockIdx.x runs over the (x, y) tiles, x fastest; blockIdx.y over z
+    const int nbx = (p.nx + TX - 1) / TX;
+    const int by = blockIdx.x / nbx, bx = blockIdx.x - by * nbx;
     tile_update<T, QG, G_SW, H_SW, HYDRO, PMRT, TY, TZ>(p, TableLat{pl.h}, TableLat{pl.g}, phi_in, phi_out, flag,
-                                                        tile, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x,
-                                                        threadIdx.y, threadIdx.z);
+                                                        tile, bx, by, blockIdx.y, threadIdx.x, threadIdx.y,
+                                                        threadIdx.z);
 }
 template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool PMRT = false>
 static cudaError_t launch(const Params &p, const Planes &pl, const float *pi, float *po, int *flag,
                           cudaStream_t st) {
     const dim3 block(TX, TY, TZ);
-    const dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + TZ - 1) / TZ);
+    const dim3 grid(((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY), (p.nz + TZ - 1) / TZ);
     fused_step_kernel<T, QG, G_SW, H_SW, HYDRO, PMRT><<<grid, block, 0, st>>>(p, pl, pi, po, flag);
     return cudaGetLastError();
 }
