@@ -372,6 +372,34 @@ def unfused_form(args, prob, phi0_dev, stream, peak, fused_ms):
     return out
 
 
+def stencil_pairs(args, prob, phi0_dev, stream, peak):
+    """The stencil pairs of Section 5.1 (phase-field lattice, hydrodynamic lattice)
+    on the same workload and GPU, FP32: MLUPS and the fraction of the HBM roof of
+    each pair's own bytes per cell, (q_phase + q_hydro) x 8 + 8."""
+    import torch
+
+    from paper_2012_06144_gb300 import lbm
+
+    out = {}
+    steps = min(args.steps, 200)
+    for qp, q in ((15, 19), (15, 27), (19, 19), (27, 27)):
+        d, prm = lbm.from_problem(prob)
+        d.q_phase, d.q_hydro = qp, q
+        sim = lbm.Simulation(d, prm, stream=stream)
+        sim.init_phase(phi0_dev)
+        sim.step(args.warmup // 10 + 3)
+        sim.synchronize()
+        ms = time_steps(sim, stream, steps) / steps
+        sim.synchronize()
+        bpc = (qp + q) * 8 + 8
+        out[f"D3Q{qp}+D3Q{q}"] = {"value": prob.ncells / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+                                  "bytes_per_cell": bpc, "roofline_frac": prob.ncells * bpc / (ms / 1e3) / 1e9 / peak}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    return out
+
+
 def rising_bubble_form(args, stream):
     """The walled 128x512x128 rising bubble (D = 32, Eo 10, Mo 1e-3, t_ref 2000)
     for args.rising_steps steps: light-phase centroid and rise velocity recorded
@@ -435,6 +463,7 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=5000, help="timed steps of the batched workload")
     ap.add_argument("--no-rising", action="store_true", help="skip the rising-bubble observables")
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused baseline")
+    ap.add_argument("--no-pairs", action="store_true", help="skip the other stencil pairs")
     ap.add_argument("--rising-steps", type=int, default=10000, help="steps of the rising-bubble run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -534,6 +563,9 @@ def main():
     unfused = None
     if rank == 0 and not args.no_unfused and args.precision == "fp32" and args.workload == "roofline":
         unfused = unfused_form(args, prob, phi0_dev, stream, peak, launch_ms)
+    pairs = None
+    if rank == 0 and not args.no_pairs and args.precision == "fp32" and args.workload == "roofline":
+        pairs = stencil_pairs(args, prob, phi0_dev, stream, peak)
     rising = None
     if rank == 0 and not args.no_rising and args.precision == "fp32" and args.workload == "roofline":
         rising = rising_bubble_form(args, stream)
@@ -551,7 +583,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
             "gpu_launches": args.steps, "precision_forms": forms, "batched_form": batched,
-            "rising_bubble": rising, "unfused_form": unfused,
+            "rising_bubble": rising, "unfused_form": unfused, "stencil_pairs": pairs,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

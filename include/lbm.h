@@ -5,7 +5,8 @@
  * Method: Holzer, Bauer, Koestler, Ruede, "Highly efficient lattice Boltzmann
  * multiphase simulations of immiscible fluids at high-density ratios on CPUs and
  * GPUs through code generation", arXiv 2012.06144.
- *   - phase-field LB on D3Q15 (Section 3.1, eq:lb_interface, eq:interfaceTracking,
+ *   - phase-field LB on D3Q15, or D3Q19 / D3Q27 for the other stencil pairs of
+ *     Section 5.1 (Section 3.1, eq:lb_interface, eq:interfaceTracking,
  *     eq:updatePhaseField), single-relaxation-time collision with rate
  *     omega_phi = 1/(3 M + 1/2);
  *   - velocity-based hydrodynamic LB on D3Q19 or D3Q27 (Section 3.2, eq:lb_flow,
@@ -88,7 +89,8 @@ typedef struct {
     int nx, ny, nz; /* cells per axis, each >= 1, nx*ny*nz < 2^31,
                        ny <= 524280, nz <= 65535 (launch-grid limits)       */
     int wall[3];    /* 0 = periodic axis, 1 = no-slip walls on both faces       */
-    int q_phase;    /* must be 15                                               */
+    int q_phase;    /* 15 (the benchmarked pair), 19 or 27; 19 and 27 need FP32
+                       storage, the SRT phase collision and the fused form      */
     int q_hydro;    /* 19 or 27                                                 */
 } lbm_domain;
 
@@ -143,7 +145,7 @@ enum {
 lbm_status lbm_workspace_size(const lbm_domain *dom, const lbm_params *prm, size_t *bytes);
 
 /* Validates the problem (Section 3 parameters; LBM_ERR_ARG on a non-positive
- * size, q_phase != 15, q_hydro not 19/27, non-positive densities, viscosities,
+ * size, q_phase not 15/19/27, q_hydro not 19/27, non-positive densities, viscosities,
  * xi or mobility, negative sigma, non-finite values), derives tau_H, tau_L,
  * omega_phi, beta, kappa and creates a handle on the current CUDA device.
  * cuda_stream: a cudaStream_t to enqueue all work on, or NULL for the legacy
@@ -173,7 +175,7 @@ lbm_status lbm_get_fields(lbm_t *s, float *phi, float *u, float *p, int on_devic
 lbm_status lbm_reduce(lbm_t *s, double *out);
 
 /* Full state at time level t, pre-collision, in the natural population layout
- * above: h = h^{t+1} (15 planes; the phase field runs one step ahead, see
+ * above: h = h^{t+1} (q_phase planes; the phase field runs one step ahead, see
  * Algorithm 2), g = g^t (q_hydro planes), phi = phi^t.  Any output may be NULL.
  * lbm_set_state takes the same three arrays (none may be NULL) and makes them
  * the current state; it also marks the handle initialised.  Checkpoint and

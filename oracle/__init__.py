@@ -61,6 +61,7 @@ class orc_problem(ctypes.Structure):
         ("theta_from_local_phi", ctypes.c_int),
         ("clamp_phi", ctypes.c_int),
         ("phase_mrt", ctypes.c_int),
+        ("q_phase", ctypes.c_int),
     ]
 
 
@@ -132,6 +133,7 @@ def make_problem(prob, theta_from_local_phi: bool = False, clamp_phi=None, phase
     p.theta_from_local_phi = int(theta_from_local_phi)
     p.clamp_phi = int(getattr(prob, "clamp_phi", 0) if clamp_phi is None else clamp_phi)
     p.phase_mrt = int(getattr(prob, "phase_mrt", 0) if phase_mrt is None else phase_mrt)
+    p.q_phase = int(getattr(prob, "q_phase", 15))
     return p
 
 
@@ -174,7 +176,7 @@ def phase_cell(p: orc_problem, h: np.ndarray, nbprev: np.ndarray, u: np.ndarray)
     h = np.ascontiguousarray(h, dtype=np.float64)
     nb = np.ascontiguousarray(nbprev, dtype=np.float64).reshape(27)
     u = np.ascontiguousarray(u, dtype=np.float64)
-    hs = np.zeros(15)
+    hs = np.zeros(p.q_phase or 15)
     phi = np.zeros(1)
     lib().orc_phase_cell(ctypes.byref(p), _dp(h), _dp(nb), _dp(u), _dp(hs), _dp(phi))
     return hs, float(phi[0])
@@ -227,7 +229,7 @@ class State:
         self.p = p
         shape = (p.nz, p.ny, p.nx)
         phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(shape)
-        self.h = np.zeros((15,) + shape)
+        self.h = np.zeros((p.q_phase or 15,) + shape)
         self.g = np.zeros((p.q_hydro,) + shape)
         self.phi_prev = np.zeros(shape)
         self.u_prev = np.zeros((3,) + shape)

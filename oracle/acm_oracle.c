@@ -27,7 +27,7 @@
  *    tau_phi = M / c_s^2 (shifted convention, as for nu = tau c_s^2 and s_nu = 1/(tau+1/2));
  *  - normal n = G/|G|, and n = 0 when |G|^2 <= 1e-24;
  *  - theta uses Phi^{k-1} at the cell (flag: the local phi_k instead);
- *  - phase gradient with D3Q15 weights, hydro gradient/Laplacian with the hydro
+ *  - phase gradient with the phase lattice's weights, hydro gradient/Laplacian with the hydro
  *    lattice's weights;
  *  - viscous force from the non-equilibrium second moments built with the
  *    velocity u' that carries all forces except F_mu itself;
@@ -131,7 +131,7 @@ int orc_lattice_table(int q, int *e, double *w, int *opp) {
 typedef struct {
     int nx, ny, nz;
     int wall[3];      /* 0: periodic axis, 1: no-slip walls on both faces     */
-    int q_hydro;      /* 19 or 27; the phase-field lattice is D3Q15           */
+    int q_hydro;      /* 19 or 27                                             */
     double rho_H, rho_L;
     double nu_H, nu_L; /* kinematic viscosities of heavy and light fluid      */
     double sigma, xi, mobility;
@@ -143,7 +143,11 @@ typedef struct {
                                  1: MRT of Section 3.1 -- first-order moments
                                  relaxed with omega_phi, all others with 1, in a
                                  weighted-orthogonal moment basis              */
+    int q_phase;              /* phase-field lattice: 15 (Section 5), 19 or 27 (the
+                                 stencil pairs of Section 5.1); 0 reads as 15  */
 } orc_problem;
+
+static int phase_q(const orc_problem *P) { return P->q_phase ? P->q_phase : 15; }
 
 typedef struct {
     double tau_H, tau_L;   /* nu = tau c_s^2 (Section 3.2)                    */
@@ -250,21 +254,22 @@ int orc_gradient_laplacian(const orc_problem *P, int q, const double *phi, doubl
 
 /* ------------------------------------------------------------------------ */
 /* Section 3.1: one phase-field collision at one cell.
- *   h      : the 15 pre-collision populations h_i^k(x)
+ *   h      : the q_phase pre-collision populations h_i^k(x)
  *   nbprev : 3x3x3 neighbourhood of the stored phase field Phi^{k-1}
  *   u      : velocity u_{k-1}(x) of the previous hydrodynamic step
  * Outputs the post-collision populations and phi_k = sum_i h_i.            */
 void orc_phase_cell(const orc_problem *P, const double *h, const double *nbprev, const double *u,
                     double *hstar, double *phi_out) {
     lattice L;
-    make_lattice(&L, 15);
+    make_lattice(&L, phase_q(P));
     derived d = derive(P);
+    const int Q = L.q;
 
     /* eq:updatePhaseField */
     double phi = 0.0;
-    for (int i = 0; i < 15; ++i) phi += h[i];
+    for (int i = 0; i < Q; ++i) phi += h[i];
 
-    /* interface normal from the isotropic gradient (eq:grad, D3Q15 weights) */
+    /* interface normal from the isotropic gradient (eq:grad, phase-lattice weights) */
     double G[3], n[3];
     stencil_gradient(&L, nbprev, G);
     double G2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
@@ -281,8 +286,8 @@ void orc_phase_cell(const orc_problem *P, const double *h, const double *nbprev,
     double theta = (1.0 - 4.0 * (phi_theta - phi0) * (phi_theta - phi0)) / P->xi;
 
     double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    double heq[15], F[15];
-    for (int i = 0; i < 15; ++i) {
+    double heq[27], F[27];
+    for (int i = 0; i < Q; ++i) {
         double eu = L.e[i][0] * u[0] + L.e[i][1] * u[1] + L.e[i][2] * u[2];
         double en = L.e[i][0] * n[0] + L.e[i][1] * n[1] + L.e[i][2] * n[2];
         /* Gamma_i (Section 3.1) and h^eq = phi Gamma_i */
@@ -293,19 +298,19 @@ void orc_phase_cell(const orc_problem *P, const double *h, const double *nbprev,
     }
     if (!P->phase_mrt) {
         /* eq:lb_interface with Omega = omega_phi * identity */
-        for (int i = 0; i < 15; ++i) hstar[i] = h[i] + d.omega_phi * (heq[i] - h[i] - 0.5 * F[i]) + F[i];
+        for (int i = 0; i < Q; ++i) hstar[i] = h[i] + d.omega_phi * (heq[i] - h[i] - 0.5 * F[i]) + F[i];
     } else {
         /* eq:lb_interface with Omega = M^-1 S M.  In a moment basis orthogonal
          * under the weights w (sum_i w_i M_ki M_li = 0 for k != l), the part of a
          * vector y in the first-order moments is w_i e_i . (sum_j e_j y_j) / c_s^2;
          * S relaxes those with omega_phi and every other moment with 1, so
          * Omega y = y - (1 - omega_phi) w_i e_i . (sum_j e_j y_j) / c_s^2. */
-        double y[15], J[3] = {0.0, 0.0, 0.0};
-        for (int i = 0; i < 15; ++i) {
+        double y[27], J[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < Q; ++i) {
             y[i] = heq[i] - h[i] - 0.5 * F[i];
             for (int a = 0; a < 3; ++a) J[a] += L.e[i][a] * y[i];
         }
-        for (int i = 0; i < 15; ++i) {
+        for (int i = 0; i < Q; ++i) {
             double eJ = L.e[i][0] * J[0] + L.e[i][1] * J[1] + L.e[i][2] * J[2];
             double Oy = y[i] - (1.0 - d.omega_phi) * L.w[i] * eJ / CS2;
             hstar[i] = h[i] + Oy + F[i];
@@ -466,15 +471,15 @@ static void stream_push(const orc_problem *P, const lattice *L, const double *fs
 void orc_phase_step(const orc_problem *P, const double *h, const double *phi_prev, const double *u_prev,
                     double *h_next, double *phi_now) {
     lattice L;
-    make_lattice(&L, 15);
+    make_lattice(&L, phase_q(P));
     long N = ncells(P);
 #pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < P->nz; ++z)
         for (int y = 0; y < P->ny; ++y)
             for (int x = 0; x < P->nx; ++x) {
                 long c = cell_index(P, x, y, z);
-                double hl[15], hs[15], nb[27], u[3], phi;
-                for (int i = 0; i < 15; ++i) hl[i] = h[(long)i * N + c];
+                double hl[27], hs[27], nb[27], u[3], phi;
+                for (int i = 0; i < L.q; ++i) hl[i] = h[(long)i * N + c];
                 gather_stencil(P, phi_prev, x, y, z, nb);
                 for (int a = 0; a < 3; ++a) u[a] = u_prev[a * N + c];
                 orc_phase_cell(P, hl, nb, u, hs, &phi);
@@ -527,12 +532,12 @@ void orc_fields(const orc_problem *P, const double *g, const double *phi, double
 /* Initial state: h_i = phi0 w_i (= phi Gamma_i at u = 0), g_i = 0 (p* = 0,
  * u = 0), Phi^{-1} = phi0, u_{-1} = 0. */
 void orc_init(const orc_problem *P, const double *phi0, double *h, double *g, double *phi_prev, double *u_prev) {
-    lattice L15, LG;
-    make_lattice(&L15, 15);
+    lattice LP, LG;
+    make_lattice(&LP, phase_q(P));
     make_lattice(&LG, P->q_hydro);
     long N = ncells(P);
     for (long c = 0; c < N; ++c) {
-        for (int i = 0; i < 15; ++i) h[(long)i * N + c] = L15.w[i] * phi0[c];
+        for (int i = 0; i < LP.q; ++i) h[(long)i * N + c] = LP.w[i] * phi0[c];
         for (int i = 0; i < LG.q; ++i) g[(long)i * N + c] = 0.0;
         phi_prev[c] = phi0[c];
         for (int a = 0; a < 3; ++a) u_prev[a * N + c] = 0.0;
@@ -543,8 +548,8 @@ void orc_init(const orc_problem *P, const double *phi0, double *h, double *g, do
  * Algorithm 2: phase step, then hydro step. */
 int orc_run(const orc_problem *P, double *h, double *g, double *phi_prev, double *u_prev, long nsteps) {
     long N = ncells(P);
-    int Q = P->q_hydro;
-    double *h2 = malloc(sizeof(double) * 15 * N);
+    int Q = P->q_hydro, QP = phase_q(P);
+    double *h2 = malloc(sizeof(double) * QP * N);
     double *g2 = malloc(sizeof(double) * Q * N);
     double *phi_now = malloc(sizeof(double) * N);
     if (!h2 || !g2 || !phi_now) {
@@ -556,7 +561,7 @@ int orc_run(const orc_problem *P, double *h, double *g, double *phi_prev, double
     for (long k = 0; k < nsteps; ++k) {
         orc_phase_step(P, h, phi_prev, u_prev, h2, phi_now);
         orc_hydro_step(P, g, phi_now, g2, u_prev);
-        memcpy(h, h2, sizeof(double) * 15 * N);
+        memcpy(h, h2, sizeof(double) * QP * N);
         memcpy(g, g2, sizeof(double) * Q * N);
         memcpy(phi_prev, phi_now, sizeof(double) * N);
     }

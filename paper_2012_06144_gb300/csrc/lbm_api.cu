@@ -32,7 +32,7 @@ Layout layout(const lbm_domain &d, int precision, int form) {
     L.h_rest = off;
     off += N * sizeof(float);
     L.h_mov = off;
-    off = align256(off + 14 * N * b);
+    off = align256(off + (size_t)(d.q_phase - 1) * N * b);
     L.g_rest = off;
     off += N * sizeof(float);
     L.g_mov = off;
@@ -50,7 +50,7 @@ Layout layout(const lbm_domain &d, int precision, int form) {
     L.h_tmp = L.g_tmp = L.u = 0;
     if (form == LBM_FORM_UNFUSED) {  // second grid of both lattices, stored velocity
         L.h_tmp = off;
-        off = align256(off + 15 * N * sizeof(float));
+        off = align256(off + (size_t)d.q_phase * N * sizeof(float));
         L.g_tmp = off;
         off = align256(off + (size_t)d.q_hydro * N * sizeof(float));
         L.u = off;
@@ -70,7 +70,8 @@ lbm_status validate(const lbm_domain *d, const lbm_params *p, std::string &why) 
     if (d->nz > 65535 || d->ny > 8 * 65535) return why = "nz must be <= 65535 and ny <= 524280", LBM_ERR_ARG;
     for (int a = 0; a < 3; ++a)
         if (d->wall[a] != 0 && d->wall[a] != 1) return why = "wall[a] must be 0 (periodic) or 1 (walls)", LBM_ERR_ARG;
-    if (d->q_phase != 15) return why = "q_phase must be 15 (D3Q15 phase-field lattice)", LBM_ERR_ARG;
+    if (d->q_phase != 15 && d->q_phase != 19 && d->q_phase != 27)
+        return why = "q_phase must be 15, 19 or 27", LBM_ERR_ARG;
     if (d->q_hydro != 19 && d->q_hydro != 27) return why = "q_hydro must be 19 or 27", LBM_ERR_ARG;
     const double vals[] = {p->rho_H, p->rho_ratio, p->nu_H, p->mu_ratio, p->sigma, p->xi, p->mobility,
                            p->gravity[0], p->gravity[1], p->gravity[2], p->rho_ref};
@@ -99,6 +100,9 @@ lbm_status validate(const lbm_domain *d, const lbm_params *p, std::string &why) 
         return why = "kernel_form must be LBM_FORM_FUSED or LBM_FORM_UNFUSED", LBM_ERR_ARG;
     if (p->kernel_form == LBM_FORM_UNFUSED && p->precision != LBM_PRECISION_FP32)
         return why = "the unfused form is built for FP32 storage", LBM_ERR_ARG;
+    if (d->q_phase != 15 && (p->precision != LBM_PRECISION_FP32 || p->phase_collision != LBM_PHASE_SRT ||
+                             p->kernel_form != LBM_FORM_FUSED))
+        return why = "the D3Q19 / D3Q27 phase lattices run with FP32 storage, SRT, fused form", LBM_ERR_ARG;
     const double rho_L = p->rho_H / p->rho_ratio;
     const double nu_L = p->nu_H * p->rho_H / (p->mu_ratio * rho_L);
     if (!(rho_L > 0) || !finite(rho_L)) return why = "rho_L = rho_H / rho_ratio must be positive", LBM_ERR_ARG;
@@ -281,7 +285,7 @@ lbm_status lbm_init_phase(lbm_t *s, const float *phi0, int phi0_on_device) {
     DeviceGuard dg(s->device);
     LBM_CK(s, cudaMemcpyAsync(s->phi[0], phi0, plane_bytes(s), kind_to_device(phi0_on_device), s->stream));
     if (!phi0_on_device) LBM_CK(s, cudaStreamSynchronize(s->stream));
-    LBM_CK(s, lbm::launch_init(s->kp, s->sto, s->dom.q_hydro, s->phi[0], s->stream));
+    LBM_CK(s, lbm::launch_init(s->kp, s->sto, s->dom.q_hydro, s->dom.q_phase, s->phi[0], s->stream));
     LBM_CK(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
     // time level 0: the first phase-field step alone (u_{-1} = 0, phi^{-1} = phi0)
     if (s->unfused) {
@@ -289,7 +293,7 @@ lbm_status lbm_init_phase(lbm_t *s, const float *phi0, int phi0_on_device) {
         LBM_CK(s, lbm::launch_unfused(s->kp, s->uf, s->sto, s->dom.q_hydro, false, s->phi[0], s->phi[1], s->flag,
                                       s->stream));
     } else {
-        LBM_CK(s, lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, false, false, false, s->phi[0], s->phi[1],
+        LBM_CK(s, lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, s->dom.q_phase, false, false, false, s->phi[0], s->phi[1],
                                    s->flag, s->stream));
     }
     s->cur = 1;
@@ -307,7 +311,7 @@ lbm_status lbm_step(lbm_t *s, int64_t n) {
             LBM_CK(s, lbm::launch_unfused(s->kp, s->uf, s->sto, s->dom.q_hydro, true, s->phi[s->cur],
                                           s->phi[s->cur ^ 1], s->flag, s->stream));
         else
-            LBM_CK(s, lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, g_swapped(s), h_swapped(s), true,
+            LBM_CK(s, lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, s->dom.q_phase, g_swapped(s), h_swapped(s), true,
                                        s->phi[s->cur], s->phi[s->cur ^ 1], s->flag, s->stream));
         s->cur ^= 1;
         s->t += 1;
@@ -363,18 +367,18 @@ lbm_status lbm_get_state(lbm_t *s, float *h, float *g, float *phi, int on_device
     const size_t N = (size_t)s->kp.N;
     const int Q = s->dom.q_hydro;
     if (on_device) {
-        if (h) LBM_CK(s, lbm::launch_gather(s->kp, s->sto, 15, h_swapped(s), 0, 15, h, s->stream));
-        if (g) LBM_CK(s, lbm::launch_gather(s->kp, s->sto, Q, g_swapped(s), 0, Q, g, s->stream));
+        if (h) LBM_CK(s, lbm::launch_gather(s->kp, s->sto, true, s->dom.q_phase, h_swapped(s), 0, s->dom.q_phase, h, s->stream));
+        if (g) LBM_CK(s, lbm::launch_gather(s->kp, s->sto, false, Q, g_swapped(s), 0, Q, g, s->stream));
         if (phi) LBM_CK(s, cudaMemcpyAsync(phi, s->phi[s->cur], plane_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
         return LBM_OK;
     }
     float *stage = s->phi[s->cur ^ 1];
-    for (int i = 0; h && i < 15; ++i) {
-        LBM_CK(s, lbm::launch_gather(s->kp, s->sto, 15, h_swapped(s), i, i + 1, stage, s->stream));
+    for (int i = 0; h && i < s->dom.q_phase; ++i) {
+        LBM_CK(s, lbm::launch_gather(s->kp, s->sto, true, s->dom.q_phase, h_swapped(s), i, i + 1, stage, s->stream));
         LBM_CK(s, cudaMemcpyAsync(h + i * N, stage, plane_bytes(s), cudaMemcpyDeviceToHost, s->stream));
     }
     for (int i = 0; g && i < Q; ++i) {
-        LBM_CK(s, lbm::launch_gather(s->kp, s->sto, Q, g_swapped(s), i, i + 1, stage, s->stream));
+        LBM_CK(s, lbm::launch_gather(s->kp, s->sto, false, Q, g_swapped(s), i, i + 1, stage, s->stream));
         LBM_CK(s, cudaMemcpyAsync(g + i * N, stage, plane_bytes(s), cudaMemcpyDeviceToHost, s->stream));
     }
     if (phi) LBM_CK(s, cudaMemcpyAsync(phi, s->phi[s->cur], plane_bytes(s), cudaMemcpyDeviceToHost, s->stream));
@@ -390,18 +394,18 @@ lbm_status lbm_set_state(lbm_t *s, const float *h, const float *g, const float *
     // the state becomes time level 0: g natural, h one AA step ahead (swapped)
     s->t = 0;
     if (on_device) {
-        LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, 15, h_swapped(s), 0, 15, h, s->stream));
-        LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, Q, g_swapped(s), 0, Q, g, s->stream));
+        LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, true, s->dom.q_phase, h_swapped(s), 0, s->dom.q_phase, h, s->stream));
+        LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, false, Q, g_swapped(s), 0, Q, g, s->stream));
         LBM_CK(s, cudaMemcpyAsync(s->phi[s->cur], phi, plane_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
     } else {
         float *stage = s->phi[s->cur ^ 1];
-        for (int i = 0; i < 15; ++i) {
+        for (int i = 0; i < s->dom.q_phase; ++i) {
             LBM_CK(s, cudaMemcpyAsync(stage, h + i * N, plane_bytes(s), cudaMemcpyHostToDevice, s->stream));
-            LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, 15, h_swapped(s), i, i + 1, stage, s->stream));
+            LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, true, s->dom.q_phase, h_swapped(s), i, i + 1, stage, s->stream));
         }
         for (int i = 0; i < Q; ++i) {
             LBM_CK(s, cudaMemcpyAsync(stage, g + i * N, plane_bytes(s), cudaMemcpyHostToDevice, s->stream));
-            LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, Q, g_swapped(s), i, i + 1, stage, s->stream));
+            LBM_CK(s, lbm::launch_scatter(s->kp, s->sto, false, Q, g_swapped(s), i, i + 1, stage, s->stream));
         }
         LBM_CK(s, cudaMemcpyAsync(s->phi[s->cur], phi, plane_bytes(s), cudaMemcpyHostToDevice, s->stream));
         LBM_CK(s, cudaStreamSynchronize(s->stream));

@@ -44,27 +44,37 @@ static dim3 grid3d(const Params &p) { return dim3((p.nx + 31) / 32, (p.ny + 7) /
 
 // ---------------------------------------------------------------------------
 // h_i = w_i phi0 (= phi0 Gamma_i at u = 0, Section 3.1), g_i = 0 (p* = 0, u = 0).
-template <typename T, int QG>
+template <typename T, int QG, int QP>
 __global__ void init_kernel(long long N, const float *__restrict__ phi0, LatView<T> h, LatView<T> g) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const float f = phi0[c];
 #pragma unroll
-        for (int i = 0; i < 15; ++i) h.template store<15>(i, i, c, wgt<15>(i) * f);
+        for (int i = 0; i < QP; ++i) h.template store<QP>(i, i, c, wgt<QP>(i) * f);
 #pragma unroll
         for (int i = 0; i < QG; ++i) g.template store<QG>(i, i, c, 0.f);
     }
 }
 
-cudaError_t launch_init(const Params &p, const Storage &sto, int q, const float *phi0, cudaStream_t st) {
-    LBM_BY_PRECISION(sto, {
-        if (q == 19)
-            init_kernel<T, 19><<<grid1d(p.N), 256, 0, st>>>(p.N, phi0, h_view<T>(p, sto), g_view<T>(p, sto));
-        else if (q == 27)
-            init_kernel<T, 27><<<grid1d(p.N), 256, 0, st>>>(p.N, phi0, h_view<T>(p, sto), g_view<T>(p, sto));
-        else
-            return cudaErrorInvalidValue;
-    })
+template <typename T, int QP>
+static cudaError_t launch_init_q(const Params &p, const Storage &sto, int q, const float *phi0, cudaStream_t st) {
+    if (q == 19)
+        init_kernel<T, 19, QP><<<grid1d(p.N), 256, 0, st>>>(p.N, phi0, h_view<T>(p, sto), g_view<T>(p, sto));
+    else if (q == 27)
+        init_kernel<T, 27, QP><<<grid1d(p.N), 256, 0, st>>>(p.N, phi0, h_view<T>(p, sto), g_view<T>(p, sto));
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
+}
+
+cudaError_t launch_init(const Params &p, const Storage &sto, int q, int q_phase, const float *phi0, cudaStream_t st) {
+    if (q_phase != 15) {  // the other phase lattices run with FP32 storage
+        if (sto.precision != LBM_PRECISION_FP32) return cudaErrorInvalidValue;
+        if (q_phase == 19) return launch_init_q<float, 19>(p, sto, q, phi0, st);
+        if (q_phase == 27) return launch_init_q<float, 27>(p, sto, q, phi0, st);
+        return cudaErrorInvalidValue;
+    }
+    LBM_BY_PRECISION(sto, { return launch_init_q<T, 15>(p, sto, q, phi0, st); })
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -169,30 +179,31 @@ static void transfer_q(const Params &p, const LatView<T> &A, bool gather, bool s
     }
 }
 
-static cudaError_t transfer(const Params &p, const Storage &sto, int q, bool gather, bool sw, int i0, int i1,
-                            float *buf, cudaStream_t st) {
+static cudaError_t transfer(const Params &p, const Storage &sto, bool is_h, int q, bool gather, bool sw, int i0,
+                            int i1, float *buf, cudaStream_t st) {
     if (i0 < 0 || i1 > q || i0 >= i1) return cudaErrorInvalidValue;
     LBM_BY_PRECISION(sto, {
+        const LatView<T> A = is_h ? h_view<T>(p, sto) : g_view<T>(p, sto);
         if (q == 15)
-            transfer_q<T, 15>(p, h_view<T>(p, sto), gather, sw, i0, i1, buf, st);
+            transfer_q<T, 15>(p, A, gather, sw, i0, i1, buf, st);
         else if (q == 19)
-            transfer_q<T, 19>(p, g_view<T>(p, sto), gather, sw, i0, i1, buf, st);
+            transfer_q<T, 19>(p, A, gather, sw, i0, i1, buf, st);
         else if (q == 27)
-            transfer_q<T, 27>(p, g_view<T>(p, sto), gather, sw, i0, i1, buf, st);
+            transfer_q<T, 27>(p, A, gather, sw, i0, i1, buf, st);
         else
             return cudaErrorInvalidValue;
     })
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const Params &p, const Storage &sto, int q, bool sw, int i0, int i1, float *out,
+cudaError_t launch_gather(const Params &p, const Storage &sto, bool is_h, int q, bool sw, int i0, int i1, float *out,
                           cudaStream_t st) {
-    return transfer(p, sto, q, true, sw, i0, i1, out, st);
+    return transfer(p, sto, is_h, q, true, sw, i0, i1, out, st);
 }
 
-cudaError_t launch_scatter(const Params &p, const Storage &sto, int q, bool sw, int i0, int i1, const float *in,
-                           cudaStream_t st) {
-    return transfer(p, sto, q, false, sw, i0, i1, const_cast<float *>(in), st);
+cudaError_t launch_scatter(const Params &p, const Storage &sto, bool is_h, int q, bool sw, int i0, int i1,
+                           const float *in, cudaStream_t st) {
+    return transfer(p, sto, is_h, q, false, sw, i0, i1, const_cast<float *>(in), st);
 }
 
 // ---------------------------------------------------------------------------

@@ -36,7 +36,8 @@ constexpr int kGraphSteps = 16;
 
 struct MemberDesc {
     Params p;
-    Planes pl;
+    void *h[15];  // plane pointers of the D3Q15 phase-field lattice
+    void *g[27];  // and of the hydrodynamic lattice (slots >= q_hydro unused)
     float *phi[2];
     int *flag;
 };
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
     __shared__ float tile[TZ + 2][TY + 2][TX + 2];
     const int4 e = tiles[blockIdx.x];
     const MemberDesc &d = a.m[e.x];
-    tile_update<float, QG, G_SW, H_SW, true, false, TY, TZ>(d.p, TableLat{d.pl.h}, TableLat{d.pl.g}, d.phi[cur],
+    tile_update<float, QG, 15, G_SW, H_SW, true, false, TY, TZ>(d.p, TableLat{d.h}, TableLat{d.g}, d.phi[cur],
                                                             d.phi[cur ^ 1], d.flag, tile, e.y, e.z, e.w,
                                                             threadIdx.x, threadIdx.y, threadIdx.z);
 }
@@ -281,6 +282,8 @@ lbm_status lbm_batch_create(lbm_batch_t **out, int count, const lbm_domain *doms
             return lbm::set_thread_error("batched stepping supports the SRT phase collision only"), LBM_ERR_ARG;
         if (prms[i].kernel_form != LBM_FORM_FUSED)
             return lbm::set_thread_error("batched stepping runs the fused form only"), LBM_ERR_ARG;
+        if (doms[i].q_phase != 15)
+            return lbm::set_thread_error("batched stepping takes the D3Q15 phase-field lattice"), LBM_ERR_ARG;
     }
     if (workspace) {
         size_t need = 0;
@@ -319,11 +322,11 @@ lbm_status lbm_batch_create(lbm_batch_t **out, int count, const lbm_domain *doms
         lbm::MemberDesc &d = b->groups[i / lbm::kGroup].m[i % lbm::kGroup];
         d = lbm::MemberDesc{};
         d.p = s->kp;
-        d.pl.h[0] = s->sto.h.rest;
-        for (int k = 1; k < 15; ++k) d.pl.h[k] = static_cast<float *>(s->sto.h.mov) + (size_t)(k - 1) * s->kp.N;
-        d.pl.g[0] = s->sto.g.rest;
+        d.h[0] = s->sto.h.rest;
+        for (int k = 1; k < 15; ++k) d.h[k] = static_cast<float *>(s->sto.h.mov) + (size_t)(k - 1) * s->kp.N;
+        d.g[0] = s->sto.g.rest;
         for (int k = 1; k < 27; ++k)
-            d.pl.g[k] = k < b->q_hydro ? static_cast<float *>(s->sto.g.mov) + (size_t)(k - 1) * s->kp.N : nullptr;
+            d.g[k] = k < b->q_hydro ? static_cast<float *>(s->sto.g.mov) + (size_t)(k - 1) * s->kp.N : nullptr;
         d.phi[0] = s->phi[0];
         d.phi[1] = s->phi[1];
         d.flag = s->flag;

@@ -36,21 +36,22 @@ cudaError_t launch_unfused(const Params &p, const Unfused &uf, const Storage &st
 // One launch of the fused kernel K_k = hydro(k-1) + phase(k) (hydro = true), or
 // the first phase step alone (hydro = false).  g_swapped / h_swapped give the
 // current AA layout of each lattice.
-cudaError_t launch_step(const Params &p, const Storage &sto, int q_hydro, bool g_swapped, bool h_swapped,
-                        bool hydro, const float *phi_in, float *phi_out, int *flag, cudaStream_t st);
+cudaError_t launch_step(const Params &p, const Storage &sto, int q_hydro, int q_phase, bool g_swapped,
+                        bool h_swapped, bool hydro, const float *phi_in, float *phi_out, int *flag, cudaStream_t st);
 
 // h_i = w_i phi0, g_i = 0 (natural layout).
-cudaError_t launch_init(const Params &p, const Storage &sto, int q_hydro, const float *phi0, cudaStream_t st);
+cudaError_t launch_init(const Params &p, const Storage &sto, int q_hydro, int q_phase, const float *phi0,
+                        cudaStream_t st);
 
 // phi, u (three planes), p from (g^t, phi^t); outputs may be null.
 cudaError_t launch_fields(const Params &p, const Storage &sto, int q_hydro, bool g_swapped, const float *phi,
                           float *out_phi, float *ux, float *uy, float *uz, float *pr, cudaStream_t st);
 
-// Natural-layout planes [i0, i1) of one lattice (q = 15: h, else g) to/from a
-// dense FP32 buffer.
-cudaError_t launch_gather(const Params &p, const Storage &sto, int q, bool swapped, int i0, int i1, float *out,
-                          cudaStream_t st);
-cudaError_t launch_scatter(const Params &p, const Storage &sto, int q, bool swapped, int i0, int i1,
+// Natural-layout planes [i0, i1) of one lattice (is_h: the phase-field lattice h
+// with q = q_phase, else g with q = q_hydro) to/from a dense FP32 buffer.
+cudaError_t launch_gather(const Params &p, const Storage &sto, bool is_h, int q, bool swapped, int i0, int i1,
+                          float *out, cudaStream_t st);
+cudaError_t launch_scatter(const Params &p, const Storage &sto, bool is_h, int q, bool swapped, int i0, int i1,
                            const float *in, cudaStream_t st);
 
 // Diagnostics: LBM_DIAG_COUNT raw sums / max into out (device); scratch holds

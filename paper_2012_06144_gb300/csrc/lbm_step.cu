@@ -12,103 +12,110 @@
 //               hydro part in registers, SRT collision (eq:lb_interface), AA
 //               streaming of h.
 // The same stencil field phi^{k-1} serves both halves, so one pass reads
-// 15 h + q g + phi and writes 15 h + q g + phi per cell, and no velocity field is
-// stored.  The h lattice runs one time level ahead of g.
+// q_p h + q g + phi and writes q_p h + q g + phi per cell, and no velocity field is
+// stored.  The h lattice runs one time level ahead of g.  The phase-field lattice
+// is D3Q15 (the benchmarked pair of Section 5); D3Q19 and D3Q27 give the other
+// stencil pairs of Section 5.1 (FP32 storage).
 //
 // Layout of the work: a block owns a 32 x 2 x 4 tile of cells (one warp = 32
 // consecutive x, so every population plane is read and written in full 128-byte
 // lines).  The warps first issue the row loads of the phi tile with its one-cell
-// halo, then each thread the loads of its 15 + q populations; the tile then goes
+// halo, then each thread the loads of its q_p + q populations; the tile then goes
 // to shared memory, so the stencil values never occupy in-flight registers.  The
-// per-tile body lives in lbm_step_impl.cuh, shared with the batched kernel.  Population addresses are plane base
-// (a kernel parameter) + 4 (X[dx] + Y[dy] + Z[dz]), with the per-axis neighbour
-// offsets X, Y, Z computed once per thread (periodic wrap folded in); only blocks
-// that touch a walled face evaluate the bounce-back conditions.
+// per-tile body lives in lbm_step_impl.cuh, shared with the batched kernel.
+// Population addresses are plane base (a kernel parameter) + 4 (X[dx] + Y[dy] +
+// Z[dz]), with the per-axis neighbour offsets X, Y, Z computed once per thread
+// (periodic wrap folded in); only blocks that touch a walled face evaluate the
+// bounce-back conditions.
 #include "lbm_step_impl.cuh"
 
 namespace lbm {
 
 constexpr int TY = LBM_TY, TZ = LBM_TZ;
 
-template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool PMRT>
-__global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
+// Resident blocks per SM the register budget is sized for: 4 (64 registers), or 3
+// (80 registers) when the two lattices hold 46 populations or more (D3Q27 with D3Q19
+// or D3Q27 would spill heavily at 64).
+template <int QG, int QP>
+constexpr int min_blocks() { return QG + QP >= 46 ? 3 : LBM_MIN_BLOCKS; }
+
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT>
+__global__ void __launch_bounds__(TX *TY *TZ, min_blocks<QG, QP>())
     fused_step_kernel(Params p, Planes pl, const float *__restrict__ phi_in, float *__restrict__ phi_out,
                       int *__restrict__ flag) {
     __shared__ float tile[TZ + 2][TY + 2][TX + 2];
     // blockIdx.x runs over the (x, y) tiles, x fastest; blockIdx.y over z
     const int nbx = (p.nx + TX - 1) / TX;
     const int by = blockIdx.x / nbx, bx = blockIdx.x - by * nbx;
-    tile_update<T, QG, G_SW, H_SW, HYDRO, PMRT, TY, TZ>(p, TableLat{pl.h}, TableLat{pl.g}, phi_in, phi_out, flag,
-                                                        tile, bx, by, blockIdx.y, threadIdx.x, threadIdx.y,
-                                                        threadIdx.z);
+    tile_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, TY, TZ>(p, TableLat{pl.h}, TableLat{pl.g}, phi_in, phi_out,
+                                                            flag, tile, bx, by, blockIdx.y, threadIdx.x,
+                                                            threadIdx.y, threadIdx.z);
 }
-template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool PMRT = false>
+
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT>
 static cudaError_t launch(const Params &p, const Planes &pl, const float *pi, float *po, int *flag,
                           cudaStream_t st) {
     const dim3 block(TX, TY, TZ);
     const dim3 grid(((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY), (p.nz + TZ - 1) / TZ);
-    fused_step_kernel<T, QG, G_SW, H_SW, HYDRO, PMRT><<<grid, block, 0, st>>>(p, pl, pi, po, flag);
+    fused_step_kernel<T, QG, QP, G_SW, H_SW, HYDRO, PMRT><<<grid, block, 0, st>>>(p, pl, pi, po, flag);
     return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t launch_typed(const Params &p, const Storage &sto, int q_hydro, bool g_sw, bool h_sw, bool hydro,
-                                const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
-    Planes pl;
-    pl.h[0] = sto.h.rest;
-    for (int i = 1; i < 15; ++i) pl.h[i] = static_cast<T *>(sto.h.mov) + (size_t)(i - 1) * p.N;
-    pl.g[0] = sto.g.rest;
-    for (int i = 1; i < 27; ++i) pl.g[i] = i < q_hydro ? static_cast<T *>(sto.g.mov) + (size_t)(i - 1) * p.N : nullptr;
-    if (!hydro) {
-        if (h_sw) return cudaErrorInvalidValue;  // the first phase step starts from natural h
-        return launch<T, 19, false, false, false>(p, pl, phi_in, phi_out, flag, st);
-    }
-    if (g_sw == h_sw) return cudaErrorInvalidValue;  // h runs one AA step ahead of g
-    if (q_hydro == 19)
-        return g_sw ? launch<T, 19, true, false, true>(p, pl, phi_in, phi_out, flag, st)
-                    : launch<T, 19, false, true, true>(p, pl, phi_in, phi_out, flag, st);
-    if (q_hydro == 27)
-        return g_sw ? launch<T, 27, true, false, true>(p, pl, phi_in, phi_out, flag, st)
-                    : launch<T, 27, false, true, true>(p, pl, phi_in, phi_out, flag, st);
-    return cudaErrorInvalidValue;
-}
-
-// The MRT phase collision (FP32 storage only).
-static cudaError_t launch_mrt(const Params &p, const Storage &sto, int q_hydro, bool g_sw, bool h_sw, bool hydro,
-                              const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
-    Planes pl;
-    pl.h[0] = sto.h.rest;
-    for (int i = 1; i < 15; ++i) pl.h[i] = static_cast<float *>(sto.h.mov) + (size_t)(i - 1) * p.N;
-    pl.g[0] = sto.g.rest;
-    for (int i = 1; i < 27; ++i)
-        pl.g[i] = i < q_hydro ? static_cast<float *>(sto.g.mov) + (size_t)(i - 1) * p.N : nullptr;
+// The layouts of one time step: g natural and h swapped, or g swapped and h
+// natural (h runs one AA step ahead); the first phase step alone (no hydro)
+// starts from natural h.
+template <typename T, int QP, bool PMRT>
+static cudaError_t launch_layouts(const Params &p, const Planes &pl, int q_hydro, bool g_sw, bool h_sw, bool hydro,
+                                  const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
     if (!hydro) {
         if (h_sw) return cudaErrorInvalidValue;
-        return launch<float, 19, false, false, false, true>(p, pl, phi_in, phi_out, flag, st);
+        return launch<T, 19, QP, false, false, false, PMRT>(p, pl, phi_in, phi_out, flag, st);
     }
     if (g_sw == h_sw) return cudaErrorInvalidValue;
     if (q_hydro == 19)
-        return g_sw ? launch<float, 19, true, false, true, true>(p, pl, phi_in, phi_out, flag, st)
-                    : launch<float, 19, false, true, true, true>(p, pl, phi_in, phi_out, flag, st);
+        return g_sw ? launch<T, 19, QP, true, false, true, PMRT>(p, pl, phi_in, phi_out, flag, st)
+                    : launch<T, 19, QP, false, true, true, PMRT>(p, pl, phi_in, phi_out, flag, st);
     if (q_hydro == 27)
-        return g_sw ? launch<float, 27, true, false, true, true>(p, pl, phi_in, phi_out, flag, st)
-                    : launch<float, 27, false, true, true, true>(p, pl, phi_in, phi_out, flag, st);
+        return g_sw ? launch<T, 27, QP, true, false, true, PMRT>(p, pl, phi_in, phi_out, flag, st)
+                    : launch<T, 27, QP, false, true, true, PMRT>(p, pl, phi_in, phi_out, flag, st);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_step(const Params &p, const Storage &sto, int q_hydro, bool g_sw, bool h_sw, bool hydro,
-                        const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
-    if (p.phase_mrt) {
+template <typename T>
+static Planes planes_of(const Params &p, const Storage &sto, int q_hydro, int q_phase) {
+    Planes pl;
+    pl.h[0] = sto.h.rest;
+    for (int i = 1; i < 27; ++i) pl.h[i] = i < q_phase ? static_cast<T *>(sto.h.mov) + (size_t)(i - 1) * p.N : nullptr;
+    pl.g[0] = sto.g.rest;
+    for (int i = 1; i < 27; ++i) pl.g[i] = i < q_hydro ? static_cast<T *>(sto.g.mov) + (size_t)(i - 1) * p.N : nullptr;
+    return pl;
+}
+
+cudaError_t launch_step(const Params &p, const Storage &sto, int q_hydro, int q_phase, bool g_sw, bool h_sw,
+                        bool hydro, const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
+    // the MRT phase collision and the D3Q19 / D3Q27 phase lattices: FP32 storage
+    if (p.phase_mrt || q_phase != 15) {
         if (sto.precision != LBM_PRECISION_FP32) return cudaErrorInvalidValue;
-        return launch_mrt(p, sto, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
+        const Planes pl = planes_of<float>(p, sto, q_hydro, q_phase);
+        if (p.phase_mrt && q_phase == 15)
+            return launch_layouts<float, 15, true>(p, pl, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
+        if (p.phase_mrt) return cudaErrorInvalidValue;
+        if (q_phase == 19)
+            return launch_layouts<float, 19, false>(p, pl, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
+        if (q_phase == 27)
+            return launch_layouts<float, 27, false>(p, pl, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
+        return cudaErrorInvalidValue;
     }
     switch (sto.precision) {
         case LBM_PRECISION_FP32:
-            return launch_typed<float>(p, sto, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
+            return launch_layouts<float, 15, false>(p, planes_of<float>(p, sto, q_hydro, 15), q_hydro, g_sw, h_sw,
+                                                    hydro, phi_in, phi_out, flag, st);
         case LBM_PRECISION_FP16:
-            return launch_typed<__half>(p, sto, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
+            return launch_layouts<__half, 15, false>(p, planes_of<__half>(p, sto, q_hydro, 15), q_hydro, g_sw, h_sw,
+                                                     hydro, phi_in, phi_out, flag, st);
         case LBM_PRECISION_BF16:
-            return launch_typed<__nv_bfloat16>(p, sto, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
+            return launch_layouts<__nv_bfloat16, 15, false>(p, planes_of<__nv_bfloat16>(p, sto, q_hydro, 15), q_hydro,
+                                                            g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
         default:
             return cudaErrorInvalidValue;
     }

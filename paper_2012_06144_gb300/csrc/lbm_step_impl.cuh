@@ -33,9 +33,16 @@ constexpr int TX = 32;  // one warp = 32 consecutive x
 // Plane pointers of both lattices: slot 0 (rest) is FP32, slots >= 1 hold the
 // moving populations in the storage type of the launch.
 struct Planes {
-    void *h[15];
+    void *h[27];
     void *g[27];
 };
+
+// Pairwise sum a[LO] + ... + a[LO + N - 1], halves first (a fixed association).
+template <int LO, int N>
+__device__ __forceinline__ float tree_sum(const float *a) {
+    if constexpr (N == 1) return a[LO];
+    else return tree_sum<LO, N / 2>(a) + tree_sum<LO + N / 2, N - N / 2>(a);
+}
 
 // Plane addresses of one lattice from a table of pointers (kernel parameters).
 struct TableLat {
@@ -178,7 +185,8 @@ __device__ __forceinline__ void pop_store_enc(const L &lat, const Nb3 &n, int i,
 // Collision of both lattices at one cell and the streaming stores, from the
 // pre-collision populations gv (g^{k-1}), hv (h^k) and the 3x3x3 neighbourhood nb
 // of phi^{k-1}.
-template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, bool EDGE, typename LH, typename LG>
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, bool EDGE, typename LH,
+          typename LG>
 __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh, const LG &lg, const Nb3 &n, const float *gv,
                                                   const float *hv, const float *nb, float *__restrict__ phi_out,
                                                   int *__restrict__ flag) {
@@ -214,18 +222,19 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh,
 
     // ---- phase-field step k (Section 3.1)
     // phi_k = sum_i h_i (eq:updatePhaseField), summed as a tree over opposite pairs
-    float pr[8];
+    constexpr int NPR = (QP + 1) / 2;
+    float pr[NPR];
     pr[0] = hv[0];
 #pragma unroll
-    for (int j = 0; j < 7; ++j) pr[j + 1] = hv[2 * j + 1] + hv[2 * j + 2];
-    const float phik = ((pr[0] + pr[1]) + (pr[2] + pr[3])) + ((pr[4] + pr[5]) + (pr[6] + pr[7]));
+    for (int j = 0; j < NPR - 1; ++j) pr[j + 1] = hv[2 * j + 1] + hv[2 * j + 2];
+    const float phik = tree_sum<0, NPR>(pr);
     phi_out[n.X[1]] = phik;
     if (!(fabsf(phik) < 1e30f)) *flag = 1;
 
-    // interface normal from eq:grad with D3Q15 weights (the face and corner sums
-    // of the same neighbourhood)
+    // interface normal from eq:grad with the phase lattice's weights (the class
+    // sums of the same neighbourhood)
     float Gx, Gy, Gz;
-    stencil_grad<15>(S, Gx, Gy, Gz);
+    stencil_grad<QP>(S, Gx, Gy, Gz);
     const float G2 = Gx * Gx + Gy * Gy + Gz * Gz;
     float nx = 0.f, ny = 0.f, nz = 0.f;
     if (G2 > 1e-24f) {
@@ -247,8 +256,8 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh,
     if constexpr (PMRT) {
         float jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
-        for (int i = 1; i < 15; i += 2) {
-            const V3 e = vel<15>(i);
+        for (int i = 1; i < QP; i += 2) {
+            const V3 e = vel<QP>(i);
             const float dh = hv[i] - hv[i + 1];
             jx += e.x * dh;
             jy += e.y * dh;
@@ -271,9 +280,9 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh,
     // to the rounding of small increments, i.e. the cell's phase mass is kept.
     float dsum = 0.f;
 #pragma unroll
-    for (int i = 1; i < 15; i += 2) {
-        const V3 e = vel<15>(i);
-        const float w = wgt<15>(i);
+    for (int i = 1; i < QP; i += 2) {
+        const V3 e = vel<QP>(i);
+        const float w = wgt<QP>(i);
         const float eu = e.x * ux + e.y * uy + e.z * uz;
         const float en = e.x * nx + e.y * ny + e.z * nz;
         const float pw = phik * w;
@@ -289,16 +298,16 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh,
             a += corr;
             b -= corr;
         }
-        const T qa = ch.template encode<15>(a, i), qb = ch.template encode<15>(b, i + 1);
-        pop_store_enc<T, 15, H_SW, EDGE>(lh, n, i, qa);
-        pop_store_enc<T, 15, H_SW, EDGE>(lh, n, i + 1, qb);
-        dsum += (ch.template decode<15>(qa, i) - hv[i]) + (ch.template decode<15>(qb, i + 1) - hv[i + 1]);
+        const T qa = ch.template encode<QP>(a, i), qb = ch.template encode<QP>(b, i + 1);
+        pop_store_enc<T, QP, H_SW, EDGE>(lh, n, i, qa);
+        pop_store_enc<T, QP, H_SW, EDGE>(lh, n, i + 1, qb);
+        dsum += (ch.template decode<QP>(qa, i) - hv[i]) + (ch.template decode<QP>(qb, i + 1) - hv[i + 1]);
     }
-    pop_store_rest<T, 15, H_SW, EDGE>(lh, n, hv[0] - dsum);
+    pop_store_rest<T, QP, H_SW, EDGE>(lh, n, hv[0] - dsum);
 }
 
-template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, bool EDGE, int TY, int TZ, typename LH,
-          typename LG>
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, bool EDGE, int TY, int TZ,
+          typename LH, typename LG>
 __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const LG &lg, const Nb3 &n, bool active,
                                             const float *__restrict__ phi_in, float (*tile)[TY + 2][TX + 2],
                                             float *__restrict__ phi_out, int *__restrict__ flag, int bx, int by,
@@ -332,14 +341,14 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
 
     // ---- the population loads
     const Codec<T> ch{p.h_ref, 1.0f, 1.0f}, cg{0.0f, p.g_scale, p.g_inv_scale};
-    float gv[QG], hv[15];
+    float gv[QG], hv[QP];
     if (active) {
         if (HYDRO) {
 #pragma unroll
             for (int i = 0; i < QG; ++i) gv[i] = pop_load<T, QG, G_SW, EDGE>(lg, n, i, cg);
         }
 #pragma unroll
-        for (int i = 0; i < 15; ++i) hv[i] = pop_load<T, 15, H_SW, EDGE>(lh, n, i, ch);
+        for (int i = 0; i < QP; ++i) hv[i] = pop_load<T, QP, H_SW, EDGE>(lh, n, i, ch);
     }
 
 #pragma unroll
@@ -361,13 +370,14 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx)
                 nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
-    collide_and_store<T, QG, G_SW, H_SW, HYDRO, PMRT, EDGE>(p, lh, lg, n, gv, hv, nb, phi_out, flag);
+    collide_and_store<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, EDGE>(p, lh, lg, n, gv, hv, nb, phi_out, flag);
 }
 
 // One tile (bx, by, bz) of 32 x TY x TZ cells, one thread per cell: per-thread
 // neighbour offsets, then the bounce-back-checking path only if the tile touches
 // a walled face.  Every thread of the block must call this (it synchronises).
-template <typename T, int QG, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, int TY, int TZ, typename LH, typename LG>
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, int TY, int TZ, typename LH,
+          typename LG>
 __device__ __forceinline__ void tile_update(const Params &p, const LH &lh, const LG &lg,
                                             const float *__restrict__ phi_in, float *__restrict__ phi_out,
                                             int *__restrict__ flag, float (*tile)[TY + 2][TX + 2], int bx, int by,
@@ -397,10 +407,10 @@ __device__ __forceinline__ void tile_update(const Params &p, const LH &lh, const
     const bool edge = (wx && (bx == 0 || (bx + 1) * TX >= p.nx)) || (wy && (by == 0 || (by + 1) * TY >= p.ny)) ||
                       (wz && (bz == 0 || (bz + 1) * TZ >= p.nz));
     if (edge)
-        cell_update<T, QG, G_SW, H_SW, HYDRO, PMRT, true, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, true, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
                                                             by, bz, tx, ty, tz);
     else
-        cell_update<T, QG, G_SW, H_SW, HYDRO, PMRT, false, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, false, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
                                                              by, bz, tx, ty, tz);
 }
 

@@ -152,7 +152,7 @@ def make_params(rho_H=1.0, rho_ratio=1000.0, nu_H=0.01, mu_ratio=100.0, sigma=1e
 def from_problem(prob, precision=None):
     """(lbm_domain, lbm_params) of a ``workloads.Problem``-like object; ``precision``
     ("fp32", "fp16", "bf16" or an LBM_PRECISION_* value) overrides the problem's."""
-    d = make_domain(prob.nx, prob.ny, prob.nz, prob.wall, prob.q_hydro)
+    d = make_domain(prob.nx, prob.ny, prob.nz, prob.wall, prob.q_hydro, getattr(prob, "q_phase", 15))
     prec = getattr(prob, "precision", "fp32") if precision is None else precision
     prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     p = make_params(prob.rho_H, prob.rho_ratio, prob.nu_H, prob.mu_ratio, prob.sigma, prob.xi, prob.mobility,
@@ -380,15 +380,15 @@ class Simulation:
         return dict(zip(DIAG_NAMES, lbm_reduce(self.handle)))
 
     def get_state(self, on_device: bool = False):
-        q = self.domain.q_hydro
+        q, qp = self.domain.q_hydro, self.domain.q_phase
         if on_device:
             t = self.torch
-            h = t.empty((15,) + self.shape, device=self.device)
+            h = t.empty((qp,) + self.shape, device=self.device)
             g = t.empty((q,) + self.shape, device=self.device)
             phi = t.empty(self.shape, device=self.device)
             lbm_get_state(self.handle, h.data_ptr(), g.data_ptr(), phi.data_ptr(), 1)
             return h, g, phi
-        h = np.empty((15,) + self.shape, np.float32)
+        h = np.empty((qp,) + self.shape, np.float32)
         g = np.empty((q,) + self.shape, np.float32)
         phi = np.empty(self.shape, np.float32)
         lbm_get_state(self.handle, h.ctypes.data, g.ctypes.data, phi.ctypes.data, 0)
@@ -399,7 +399,8 @@ class Simulation:
             h = np.ascontiguousarray(h, dtype=np.float32)
             g = np.ascontiguousarray(g, dtype=np.float32)
             phi = np.ascontiguousarray(phi, dtype=np.float32)
-            assert h.size == 15 * self.N and g.size == self.domain.q_hydro * self.N and phi.size == self.N
+            assert h.size == self.domain.q_phase * self.N and g.size == self.domain.q_hydro * self.N
+            assert phi.size == self.N
             lbm_set_state(self.handle, h.ctypes.data, g.ctypes.data, phi.ctypes.data, 0)
         else:
             lbm_set_state(self.handle, self._dev(h), self._dev(g), self._dev(phi), 1)

@@ -77,7 +77,7 @@ def test_workspace_size_16bit(lbm):
 
 
 @pytest.mark.parametrize("field,value", [
-    ("nx", 0), ("ny", -3), ("q_phase", 19), ("q_hydro", 15), ("q_hydro", 9), ("wall", 2),
+    ("nx", 0), ("ny", -3), ("q_phase", 21), ("q_phase", 9), ("q_hydro", 15), ("q_hydro", 9), ("wall", 2),
 ])
 def test_invalid_domain_rejected(lbm, field, value):
     d = lbm.make_domain(8, 8, 8, q_hydro=19)
@@ -211,3 +211,19 @@ def test_unfused_form_workspace_and_limits(lbm):
     with pytest.raises(lbm.LBMError) as ei:
         lbm.lbm_batch_create([d, d], [lbm.make_params(), lbm.make_params(kernel_form=lbm.LBM_FORM_UNFUSED)])
     assert ei.value.status == lbm.LBM_ERR_ARG
+
+
+def test_other_phase_lattices_limits(lbm):
+    """D3Q19 / D3Q27 phase lattices: FP32 storage, SRT, fused form, single simulations."""
+    for qp in (19, 27):
+        d = lbm.make_domain(16, 8, 4, q_hydro=27, q_phase=qp)
+        n = lbm.lbm_workspace_size(d, lbm.make_params())
+        assert n >= (qp + 27 + 2) * 16 * 8 * 4 * 4
+        for kw in (dict(precision=lbm.LBM_PRECISION_FP16), dict(phase_collision=lbm.LBM_PHASE_MRT),
+                   dict(kernel_form=lbm.LBM_FORM_UNFUSED)):
+            with pytest.raises(lbm.LBMError) as ei:
+                lbm.lbm_workspace_size(d, lbm.make_params(**kw))
+            assert ei.value.status == lbm.LBM_ERR_ARG
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_batch_create([d], [lbm.make_params()])
+        assert ei.value.status == lbm.LBM_ERR_ARG

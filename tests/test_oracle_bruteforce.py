@@ -51,7 +51,8 @@ def shifted(f, d):
 
 
 def literal_step(prob, orc, h, g, phi_prev, u_prev):
-    e15, w15, _ = orc.lattice(15)
+    qp = prob.q_phase
+    e15, w15, _ = orc.lattice(qp)
     e, w, _ = orc.lattice(prob.q_hydro)
     q = len(w)
     tau_H, tau_L = prob.nu_H / CS2, prob.nu_L / CS2
@@ -60,13 +61,13 @@ def literal_step(prob, orc, h, g, phi_prev, u_prev):
 
     # ---- phase step
     phi = h.sum(0)
-    G = sum(e15[i][:, None, None, None] * w15[i] * shifted(phi_prev, e15[i]) for i in range(15)) / CS2
+    G = sum(e15[i][:, None, None, None] * w15[i] * shifted(phi_prev, e15[i]) for i in range(qp)) / CS2
     Gn = np.sqrt((G ** 2).sum(0))
     n = np.where(Gn ** 2 > 1e-24, G / np.where(Gn > 0, Gn, 1), 0.0)
     theta = (1 - 4 * (phi_prev - 0.5) ** 2) / prob.xi
     uu = (u_prev ** 2).sum(0)
     h_next = np.zeros_like(h)
-    for i in range(15):
+    for i in range(qp):
         eu = np.einsum("a,a...->...", e15[i].astype(float), u_prev)
         Gam = w15[i] * (1 + eu / CS2 + eu ** 2 / (2 * CS2 ** 2) - uu / (2 * CS2))
         F = theta * w15[i] * np.einsum("a,a...->...", e15[i].astype(float), n)
@@ -118,14 +119,14 @@ def literal_step(prob, orc, h, g, phi_prev, u_prev):
     return h_next, phi, g_next, u
 
 
-@pytest.mark.parametrize("q", [19, 27])
-def test_literal_moment_space_step(orc, q):
-    prob = W.Problem(7, 6, 5, wall=(0, 0, 0), q_hydro=q, rho_ratio=100.0, mu_ratio=30.0, sigma=2e-3,
+@pytest.mark.parametrize("q,qp", [(19, 15), (27, 15), (19, 19), (27, 27)])
+def test_literal_moment_space_step(orc, q, qp):
+    prob = W.Problem(7, 6, 5, wall=(0, 0, 0), q_hydro=q, q_phase=qp, rho_ratio=100.0, mu_ratio=30.0, sigma=2e-3,
                      xi=3.0, mobility=0.03, gravity=(2e-5, -3e-5, 1e-5), rho_ref=0.4)
     p = orc.make_problem(prob)
     rng = np.random.default_rng(11)
     phi_prev = W.random_smooth_field(prob.shape, rng)
-    h = rng.uniform(0, 0.1, (15,) + prob.shape)
+    h = rng.uniform(0, 0.1, (qp,) + prob.shape)
     g = rng.normal(0, 1e-3, (q,) + prob.shape)
     u_prev = rng.normal(0, 1e-2, (3,) + prob.shape)
 
@@ -150,33 +151,36 @@ def test_moment_matrix_is_weighted_orthogonal(orc):
 
 def literal_phase_mrt_step(prob, orc, h, phi_prev, u_prev):
     """eq:lb_interface with Omega = M^{-1} S M literally (Section 3.1): M the
-    w-orthogonal D3Q15 moment matrix, S relaxing the first-order moments with
-    omega_phi and every other moment with 1."""
-    e15, w15, _ = orc.lattice(15)
+    w-orthogonal moment matrix of the phase lattice, S relaxing the first-order
+    moments with omega_phi and every other moment with 1."""
+    qp = prob.q_phase
+    e15, w15, _ = orc.lattice(qp)
     omega = 1.0 / (prob.mobility / CS2 + 0.5)
     M, deg = moment_matrix(e15, w15)
     Omega = np.linalg.inv(M) @ np.diag(np.where(deg == 1, omega, 1.0)) @ M
     phi = h.sum(0)
-    G = sum(e15[i][:, None, None, None] * w15[i] * shifted(phi_prev, e15[i]) for i in range(15)) / CS2
+    G = sum(e15[i][:, None, None, None] * w15[i] * shifted(phi_prev, e15[i]) for i in range(qp)) / CS2
     Gn = np.sqrt((G ** 2).sum(0))
     n = np.where(Gn ** 2 > 1e-24, G / np.where(Gn > 0, Gn, 1), 0.0)
     theta = (1 - 4 * (phi_prev - 0.5) ** 2) / prob.xi
     uu = (u_prev ** 2).sum(0)
     heq, F = np.zeros_like(h), np.zeros_like(h)
-    for i in range(15):
+    for i in range(qp):
         eu = np.einsum("a,a...->...", e15[i].astype(float), u_prev)
         heq[i] = phi * w15[i] * (1 + eu / CS2 + eu ** 2 / (2 * CS2 ** 2) - uu / (2 * CS2))
         F[i] = theta * w15[i] * np.einsum("a,a...->...", e15[i].astype(float), n)
     hs = h + np.einsum("ij,j...->i...", Omega, heq - h - 0.5 * F) + F
-    return np.array([shifted(hs[i], -e15[i]) for i in range(15)]), phi
+    return np.array([shifted(hs[i], -e15[i]) for i in range(qp)]), phi
 
 
-def test_literal_mrt_phase_step(orc):
-    prob = W.Problem(7, 6, 5, wall=(0, 0, 0), q_hydro=27, sigma=2e-3, xi=3.0, mobility=0.07, phase_mrt=1)
+@pytest.mark.parametrize("qp", [15, 19, 27])
+def test_literal_mrt_phase_step(orc, qp):
+    prob = W.Problem(7, 6, 5, wall=(0, 0, 0), q_hydro=27, q_phase=qp, sigma=2e-3, xi=3.0, mobility=0.07,
+                     phase_mrt=1)
     p = orc.make_problem(prob)
     rng = np.random.default_rng(12)
     phi_prev = W.random_smooth_field(prob.shape, rng)
-    h = rng.uniform(0, 0.1, (15,) + prob.shape)
+    h = rng.uniform(0, 0.1, (qp,) + prob.shape)
     u_prev = rng.normal(0, 1e-2, (3,) + prob.shape)
     h_lit, phi_lit = literal_phase_mrt_step(prob, orc, h, phi_prev, u_prev)
     h_next, phi_now = orc.phase_step(p, h, phi_prev, u_prev)

@@ -89,17 +89,18 @@ def test_derived_parameters(orc):
     assert d["beta"] == pytest.approx(12e-4 / 5) and d["kappa"] == pytest.approx(1.5e-4 * 5)
 
 
-def test_phase_collision_moments(orc):
+@pytest.mark.parametrize("qp", [15, 19, 27])
+def test_phase_collision_moments(orc, qp):
     """sum h* = phi; first/second moments from relaxation toward phi Gamma(u)
     plus the interface forcing, whose zeroth and second moments vanish and
-    whose first moment is c_s^2 theta n (lattice isotropy)."""
+    whose first moment is c_s^2 theta n (lattice isotropy), on each phase lattice."""
     rng = np.random.default_rng(3)
-    prob = W.Problem(4, 4, 4, xi=4.0, mobility=0.03)
+    prob = W.Problem(4, 4, 4, xi=4.0, mobility=0.03, q_phase=qp)
     p = orc.make_problem(prob)
     omega = orc.derived(p)["omega_phi"]
-    e, w, _ = orc.lattice(15)
+    e, w, _ = orc.lattice(qp)
     for trial in range(5):
-        h = rng.uniform(0, 0.2, 15)
+        h = rng.uniform(0, 0.2, qp)
         u = rng.normal(0, 0.05, 3)
         phic = rng.uniform(0.1, 0.9)
         a = rng.normal(size=3)
@@ -117,13 +118,14 @@ def test_phase_collision_moments(orc):
         assert np.abs(np.einsum("i,ia,ib->ab", hs, e, e) - exp2).max() < 1e-14
 
 
-def test_phase_normal_zero_gradient(orc):
+@pytest.mark.parametrize("qp", [15, 19, 27])
+def test_phase_normal_zero_gradient(orc, qp):
     """A flat neighbourhood has no normal: the forcing vanishes and h relaxes to phi Gamma(u)."""
-    prob = W.Problem(4, 4, 4)
+    prob = W.Problem(4, 4, 4, q_phase=qp)
     p = orc.make_problem(prob)
     omega = orc.derived(p)["omega_phi"]
-    e, w, _ = orc.lattice(15)
-    h = np.full(15, 0.05)
+    e, w, _ = orc.lattice(qp)
+    h = np.full(qp, 0.05)
     hs, phi = orc.phase_cell(p, h, np.full(27, 0.5), np.zeros(3))
     assert np.allclose(hs, (1 - omega) * h + omega * phi * w, atol=1e-15)
 
@@ -182,12 +184,14 @@ def test_hydro_forces_vanish_in_uniform_phase(orc):
     assert np.abs(gs @ e - g @ e).max() < 1e-15
 
 
-@pytest.mark.parametrize("wall", [(0, 0, 0), (1, 0, 0), (1, 1, 1), (0, 1, 0)])
-@pytest.mark.parametrize("q", [19, 27])
-def test_mass_conservation(orc, wall, q):
+@pytest.mark.parametrize("wall,q,qp", [((0, 0, 0), 19, 15), ((1, 0, 0), 19, 15), ((1, 1, 1), 19, 15),
+                                       ((0, 1, 0), 19, 15), ((0, 0, 0), 27, 15), ((1, 0, 0), 27, 15),
+                                       ((1, 1, 1), 27, 15), ((0, 1, 0), 27, 15), ((1, 1, 1), 19, 19),
+                                       ((1, 0, 1), 27, 27), ((0, 1, 0), 19, 27)])
+def test_mass_conservation(orc, wall, q, qp):
     """sum_x phi is conserved to round-off: sum_i F^phi_i = 0, the collision keeps
     the zeroth moment and streaming / bounce-back only moves populations."""
-    prob = W.Problem(11, 9, 7, wall=wall, q_hydro=q, rho_ratio=100.0, sigma=5e-4,
+    prob = W.Problem(11, 9, 7, wall=wall, q_hydro=q, q_phase=qp, rho_ratio=100.0, sigma=5e-4,
                      gravity=(0, -1e-5, 0), rho_ref=0.5)
     p = orc.make_problem(prob)
     rng = np.random.default_rng(6)

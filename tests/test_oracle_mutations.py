@@ -65,19 +65,19 @@ def _pins(orc):
         P.append(lambda q=q: I.test_stencils_exact_on_quadratics(orc, q))
     P += [
         lambda: I.test_stencil_walls_mirror(orc),
-        lambda: I.test_phase_collision_moments(orc),
-        lambda: I.test_phase_normal_zero_gradient(orc),
+        lambda: I.test_phase_collision_moments(orc, 15),
+        lambda: I.test_phase_normal_zero_gradient(orc, 15),
         lambda: I.test_hydro_collision_moments(orc, 19),
         lambda: I.test_hydro_collision_moments(orc, 27),
         lambda: I.test_hydro_forces_vanish_in_uniform_phase(orc),
         lambda: I.test_chemical_potential_vanishes_on_equilibrium_profile(orc, 27),
-        lambda: I.test_mass_conservation(orc, (1, 1, 1), 27),
+        lambda: I.test_mass_conservation(orc, (1, 1, 1), 27, 15),
         lambda: I.test_trivial_states(orc, 19),
-        lambda: Ph.test_phase_diffusion_rate(orc, 0),
-        lambda: Ph.test_phase_diffusion_rate(orc, 1),
-        lambda: B.test_literal_mrt_phase_step(orc),
+        lambda: Ph.test_phase_diffusion_rate(orc, 0, 15),
+        lambda: Ph.test_phase_diffusion_rate(orc, 1, 15),
+        lambda: B.test_literal_mrt_phase_step(orc, 15),
         lambda: Ph.test_shear_wave_viscosity(orc, 19),
-        lambda: Ph.test_planar_interface_steady(orc, 27),
+        lambda: Ph.test_planar_interface_steady(orc, 27, 15),
         lambda: Ph.test_interface_advection(orc),
         lambda: Ph.test_hydrostatic_balance(orc, 10.0),
         lambda: Ph.test_hydrostatic_balance(orc, 1000.0),

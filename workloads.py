@@ -43,6 +43,7 @@ class Problem:
     nz: int
     wall: tuple = (0, 0, 0)  # 0 = periodic axis, 1 = no-slip walls on both faces
     q_hydro: int = 27
+    q_phase: int = 15  # phase-field lattice: 15 (the benchmarked pair), 19 or 27
     rho_H: float = 1.0
     rho_ratio: float = 1000.0
     nu_H: float = 0.01
@@ -293,11 +294,12 @@ def random_smooth_field(shape, rng, modes: int = 3, lo: float = 0.0, hi: float =
 
 
 def random_state(prob: Problem, seed: int, pop_noise: float = 1e-3):
-    """A seeded state (h, g, Phi) of the library's exported layout: h (15, nz, ny, nx),
+    """A seeded state (h, g, Phi) of the library's exported layout: h (q_phase, nz, ny, nx),
     g (q_hydro, nz, ny, nx), Phi (nz, ny, nx), all float32.  Phi is a smooth field in
     [0, 1]; h and g are small random populations around a uniform rest state."""
     rng = np.random.default_rng(seed)
     phi = random_smooth_field(prob.shape, rng).astype(np.float32)
-    h = (rng.uniform(0.0, 1.0, size=(15,) + prob.shape) * (1.0 / 15.0)).astype(np.float32)
+    qp = getattr(prob, "q_phase", 15)
+    h = (rng.uniform(0.0, 1.0, size=(qp,) + prob.shape) * (1.0 / qp)).astype(np.float32)
     g = (rng.normal(0.0, pop_noise, size=(prob.q_hydro,) + prob.shape)).astype(np.float32)
     return h, g, phi
