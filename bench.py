@@ -57,15 +57,22 @@ def env_int(name, default):
         return default
 
 
-def workload(name: str, size: int = 512):
+def workload(name: str, size: int = 512, generate: bool = True):
+    """(Problem, phi0, description) of a benchmark workload; with generate=False
+    only the box and lattices (phi0 None), for the description of a run."""
     if name == "roofline":
         count = max(1, round(400 * (size / 512) ** 3))
-        prob, phi0, bubbles = W.roofline(n=size, count=count)
         desc = (f"roofline: {size}^3 triply periodic, D3Q15+D3Q27, FP32, {count} bubbles D~U[16,32] seed 6144, "
                 "rho ratio 1000, mu ratio 100, sigma 1e-4, xi 5, M 0.02, gravity Eo=10 at D=24")
+        if not generate:
+            return W.Problem(size, size, size, q_hydro=27), None, desc
+        prob, phi0, bubbles = W.roofline(n=size, count=count)
         return prob, phi0, desc
     if name == "rising_bubble":
-        prob, phi0 = W.rising_bubble()
+        if not generate:
+            prob, phi0 = W.Problem(128, 512, 128, wall=(1, 1, 1), q_hydro=27), None
+        else:
+            prob, phi0 = W.rising_bubble()
         desc = ("rising bubble: 128x512x128 walled, D3Q15+D3Q27, FP32, D=32 at (64,64,64), Eo 10, Mo 1e-3, "
                 "rho ratio 1000, mu ratio 100")
         return prob, phi0, desc
@@ -189,6 +196,14 @@ def cpu_baseline(seconds_budget: float = 20.0):
                       f"({prob.q_hydro}-velocity hydro lattice), FP64, OpenMP"}
 
 
+def run_config(args, desc, N, q, precision, world):
+    """The `config` object of the JSON line (the same on both arms)."""
+    return {"workload": desc, "cells": N, "lattices": f"D3Q15+D3Q{q}",
+            "storage": f"{precision} populations (FP32 rest), in-place AA",
+            "l2": f"state {N * (bytes_per_cell(q, precision) // 2) / 1e9:.1f} GB per GPU >> 129 MB L2, no flush needed",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     """The reference arm: the FP64 oracle timed on the host cores.  Each step is one
     oracle time step of a bounded 32^3 sample of the workload (same physics and
@@ -199,6 +214,7 @@ def run_reference(args):
     import oracle
 
     oracle.build()
+    full, _, full_desc = workload(args.workload, args.size, generate=False)
     n = 32
     prob, phi0, _ = W.roofline(n=n, count=max(1, round(400 * (n / 512) ** 3)))
     st = oracle.State(oracle.make_problem(prob), phi0)
@@ -211,10 +227,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"FP64 oracle on a {n}^3 sample of the {args.workload} workload",
-                   "cells_per_step": n ** 3},
+        "config": run_config(args, full_desc, full.ncells, full.q_hydro, "fp32", args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-                         "sample": f"{n}^3 triply periodic sample, {args.steps} steps after {args.warmup} warm-up"},
+                         "sample": f"{n}^3 triply periodic sample of the same physics and bubble recipe, each "
+                                   f"step one FP64 oracle time step; {args.steps} steps after {args.warmup} warm-up"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -576,11 +592,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": desc, "cells": N, "lattices": f"D3Q15+D3Q{q}",
-                       "storage": f"{args.precision} populations (FP32 rest), in-place AA",
-                       "l2": f"state {N * (bytes_per_cell(q, args.precision) // 2) / 1e9:.1f} GB per GPU >> 129 MB L2, "
-                             "no flush needed",
-                       "parallelism": f"replicas x{world}"},
+            "config": run_config(args, desc, N, q, args.precision, world),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
             "gpu_launches": args.steps, "precision_forms": forms, "batched_form": batched,
             "rising_bubble": rising, "unfused_form": unfused, "stencil_pairs": pairs,
