@@ -146,7 +146,7 @@ def get_threads() -> int:
 
 
 def lattice(q: int):
-    """(e (q,3) int, w (q,) float64, opp (q,) int) of D3Q15, D3Q19 or D3Q27."""
+    """(e (q,3) int, w (q,) float64, opp (q,) int) of D2Q9, D3Q15, D3Q19 or D3Q27."""
     e = np.zeros((q, 3), dtype=np.int32)
     w = np.zeros(q, dtype=np.float64)
     opp = np.zeros(q, dtype=np.int32)

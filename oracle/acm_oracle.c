@@ -54,7 +54,9 @@
 /* ------------------------------------------------------------------------ */
 /* Lattices.  Directions are numbered: rest; the six faces (+x,-x,+y,-y,+z,-z);
  * the twelve edges; the eight corners, each direction followed by its opposite.
- * D3Q19 is the first 19 of the D3Q27 list, D3Q15 is rest + faces + corners.     */
+ * D3Q19 is the first 19 of the D3Q27 list, D3Q15 is rest + faces + corners, and
+ * D2Q9 (the two-dimensional pair of Section 5.1) is rest + the four x, y faces +
+ * the four xy edges.                                                         */
 
 static const int E27[27][3] = {
     {0, 0, 0},
@@ -67,13 +69,18 @@ static const int E27[27][3] = {
 
 typedef struct {
     int q;
+    int dim; /* 3, or 2 for D2Q9 (velocities in the xy plane) */
     int e[27][3];
     double w[27];
     int opp[27];
 } lattice;
 
-/* Textbook weights of the three cubic lattices, selected by |e|^2. */
+/* Textbook weights of the lattices, selected by |e|^2. */
 static double lattice_weight(int q, int e2) {
+    if (q == 9) {
+        static const double w9[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
+        return w9[e2];
+    }
     if (q == 15) {
         static const double w15[4] = {2.0 / 9.0, 1.0 / 9.0, 0.0, 1.0 / 72.0};
         return w15[e2];
@@ -93,10 +100,14 @@ static int make_lattice(lattice *L, int q) {
         for (int i = 19; i < 27; ++i) src[n++] = i;
     } else if (q == 19 || q == 27) {
         for (int i = 0; i < q; ++i) src[n++] = i;
+    } else if (q == 9) {
+        for (int i = 0; i < 5; ++i) src[n++] = i;
+        for (int i = 7; i < 11; ++i) src[n++] = i;
     } else {
         return -1;
     }
     L->q = q;
+    L->dim = q == 9 ? 2 : 3;
     for (int i = 0; i < q; ++i) {
         const int *v = E27[src[i]];
         L->e[i][0] = v[0];
@@ -380,9 +391,9 @@ void orc_hydro_cell(const orc_problem *P, const double *g, const double *nb, dou
 
     /* eq:viscousForce: sum_i e_a e_b [Omega (g - g^eq)]_i = s_nu (m2 - m2^eq),
      * m2^eq = p* c_s^2 delta + u'u'  (second moment of g^eq) */
-    double Pi_neq[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
+    double Pi_neq[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < L.dim; ++a)
+        for (int b = 0; b < L.dim; ++b)
             Pi_neq[a][b] = m2[a][b] - (a == b ? pstar * CS2 : 0.0) - up[a] * up[b];
     double nu = tau * CS2;
     double F_mu[3];
@@ -403,10 +414,12 @@ void orc_hydro_cell(const orc_problem *P, const double *g, const double *nb, dou
      *  zeroth moment   p*            (rate 1, equilibrium p*)
      *  first moments   u + F/(2 rho) (rate 1, equilibrium u, forcing F/rho)
      *  second (Hermite) a2* = (1 - s_nu) a2 + s_nu u u
-     *  higher moments  0             (rate 1, equilibrium 0)                  */
-    double a2s[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
+     *  higher moments  0             (rate 1, equilibrium 0)
+     * The Hermite tensors run over the lattice's own dimensions (x, y for D2Q9). */
+    const int D = L.dim;
+    double a2s[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
             double a2 = m2[a][b] - (a == b ? pstar * CS2 : 0.0);
             a2s[a][b] = (1.0 - s_nu) * a2 + s_nu * u[a] * u[b];
         }
@@ -414,9 +427,9 @@ void orc_hydro_cell(const orc_problem *P, const double *g, const double *nb, dou
     for (int a = 0; a < 3; ++a) m1s[a] = u[a] + F[a] / (2.0 * rho);
     for (int i = 0; i < Q; ++i) {
         double first = 0.0, second = 0.0;
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < D; ++a) {
             first += L.e[i][a] * m1s[a];
-            for (int b = 0; b < 3; ++b)
+            for (int b = 0; b < D; ++b)
                 second += (L.e[i][a] * L.e[i][b] - (a == b ? CS2 : 0.0)) * a2s[a][b];
         }
         gstar[i] = L.w[i] * (pstar + first / CS2 + second / (2.0 * CS2 * CS2));

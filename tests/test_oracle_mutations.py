@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import test_oracle_bruteforce as B
+import test_oracle_d2q9 as D
 import test_oracle_identities as I
 import test_oracle_physics as Ph
 
@@ -54,6 +55,8 @@ MUTATIONS = [
     ("MRT phase: unweighted projection", "(1.0 - d.omega_phi) * L.w[i] * eJ / CS2",
      "(1.0 - d.omega_phi) * eJ / 10.0"),
     ("MRT phase: forcing half-step dropped", "y[i] = heq[i] - h[i] - 0.5 * F[i];", "y[i] = heq[i] - h[i];"),
+    ("D2Q9: Hermite tensors over three dimensions", "const int D = L.dim;", "const int D = 3;"),
+    ("D2Q9 diagonal weight", "{4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0}", "{4.0 / 9.0, 1.0 / 9.0, 1.0 / 18.0}"),
 ]
 
 
@@ -85,6 +88,9 @@ def _pins(orc):
         lambda: Ph.test_two_layer_poiseuille_diffuse(orc, 10.0, 1.0, 0.05, 8.0, 19, 1.5e-2),
         lambda: Ph.test_two_layer_poiseuille_diffuse(orc, 1000.0, 100.0, 0.05, 4.0, 27, 1e-2),
         lambda: Ph.test_laplace_law_cylinder(orc),
+        lambda: D.test_d2q9_lattice_moments(orc),
+        lambda: D.test_d2q9_hydro_collision_moments(orc),
+        lambda: D.test_d2q9_shear_wave_viscosity(orc),
     ]
     return P
 

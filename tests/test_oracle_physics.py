@@ -29,7 +29,7 @@ CS2 = 1.0 / 3.0
 def _equilibrium_flow(orc, s, prob, u):
     """Sets g = g^eq(p* = 0, u) and h = phi Gamma(u) (state construction only)."""
     e, w, _ = orc.lattice(prob.q_hydro)
-    eh, wh, _ = orc.lattice(15)
+    eh, wh, _ = orc.lattice(prob.q_phase)
     uu = (u ** 2).sum(0)
     eu = np.einsum("ia,a...->i...", e.astype(float), u)
     s.g[:] = w[:, None, None, None] * (3 * eu + 4.5 * eu ** 2 - 1.5 * uu)
@@ -104,8 +104,8 @@ def test_interface_advection(orc):
     assert np.abs(s.phi() - W.slab_phi(prob, 32.0, 56.0)).max() < 1.5e-2
 
 
-def _laplace_cylinder(orc, R, n=48, steps=3000, sigma=1e-3):
-    prob = W.Problem(n, n, 1, q_hydro=19, rho_ratio=1.0, mu_ratio=1.0, nu_H=0.1, sigma=sigma, xi=4.0,
+def _laplace_cylinder(orc, R, n=48, steps=3000, sigma=1e-3, q=19, qp=15):
+    prob = W.Problem(n, n, 1, q_hydro=q, q_phase=qp, rho_ratio=1.0, mu_ratio=1.0, nu_H=0.1, sigma=sigma, xi=4.0,
                      mobility=0.05)
     s = orc.State(orc.make_problem(prob), W.cylinder_phi(prob, (n / 2, n / 2), R, heavy_inside=True))
     s.run(steps)
