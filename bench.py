@@ -413,6 +413,21 @@ def stencil_pairs(args, prob, phi0_dev, stream, peak):
         sim.close()
         del sim
         torch.cuda.empty_cache()
+    # the two-dimensional pair on a box of as many cells (16 n x 32 n x 1)
+    p2, phi2 = W.roofline2d(16 * args.size, 32 * args.size)
+    sim = lbm.Simulation.from_problem(p2, stream=stream)
+    sim.init_phase(phi2)
+    sim.step(args.warmup // 10 + 3)
+    sim.synchronize()
+    ms = time_steps(sim, stream, steps) / steps
+    sim.synchronize()
+    bpc = (9 + 9) * 8 + 8
+    out["D2Q9+D2Q9"] = {"value": p2.ncells / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms, "bytes_per_cell": bpc,
+                        "roofline_frac": p2.ncells * bpc / (ms / 1e3) / 1e9 / peak,
+                        "box": f"{p2.nx}x{p2.ny}x1 periodic, circles R 12 on a pitch-64 lattice"}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
     return out
 
 

@@ -70,9 +70,14 @@ lbm_status validate(const lbm_domain *d, const lbm_params *p, std::string &why) 
     if (d->nz > 65535 || d->ny > 8 * 65535) return why = "nz must be <= 65535 and ny <= 524280", LBM_ERR_ARG;
     for (int a = 0; a < 3; ++a)
         if (d->wall[a] != 0 && d->wall[a] != 1) return why = "wall[a] must be 0 (periodic) or 1 (walls)", LBM_ERR_ARG;
-    if (d->q_phase != 15 && d->q_phase != 19 && d->q_phase != 27)
-        return why = "q_phase must be 15, 19 or 27", LBM_ERR_ARG;
-    if (d->q_hydro != 19 && d->q_hydro != 27) return why = "q_hydro must be 19 or 27", LBM_ERR_ARG;
+    if (d->q_phase != 9 && d->q_phase != 15 && d->q_phase != 19 && d->q_phase != 27)
+        return why = "q_phase must be 9, 15, 19 or 27", LBM_ERR_ARG;
+    if (d->q_hydro != 9 && d->q_hydro != 19 && d->q_hydro != 27)
+        return why = "q_hydro must be 9, 19 or 27", LBM_ERR_ARG;
+    if ((d->q_phase == 9) != (d->q_hydro == 9))
+        return why = "D2Q9 is a pair: q_phase and q_hydro both 9", LBM_ERR_ARG;
+    if (d->q_phase == 9 && (d->nz != 1 || d->wall[2] != 0))
+        return why = "the D2Q9 pair needs nz = 1 and no walls on z", LBM_ERR_ARG;
     const double vals[] = {p->rho_H, p->rho_ratio, p->nu_H, p->mu_ratio, p->sigma, p->xi, p->mobility,
                            p->gravity[0], p->gravity[1], p->gravity[2], p->rho_ref};
     for (double v : vals)
@@ -102,7 +107,9 @@ lbm_status validate(const lbm_domain *d, const lbm_params *p, std::string &why) 
         return why = "the unfused form is built for FP32 storage", LBM_ERR_ARG;
     if (d->q_phase != 15 && (p->precision != LBM_PRECISION_FP32 || p->phase_collision != LBM_PHASE_SRT ||
                              p->kernel_form != LBM_FORM_FUSED))
-        return why = "the D3Q19 / D3Q27 phase lattices run with FP32 storage, SRT, fused form", LBM_ERR_ARG;
+        return why = "the D2Q9 / D3Q19 / D3Q27 phase lattices run with FP32 storage, SRT, fused form", LBM_ERR_ARG;
+    if (d->q_phase == 9 && p->gravity[2] != 0.0)
+        return why = "the D2Q9 pair carries no z momentum: gravity[2] must be 0", LBM_ERR_ARG;
     const double rho_L = p->rho_H / p->rho_ratio;
     const double nu_L = p->nu_H * p->rho_H / (p->mu_ratio * rho_L);
     if (!(rho_L > 0) || !finite(rho_L)) return why = "rho_L = rho_H / rho_ratio must be positive", LBM_ERR_ARG;

@@ -57,7 +57,9 @@ __global__ void init_kernel(long long N, const float *__restrict__ phi0, LatView
 
 template <typename T, int QP>
 static cudaError_t launch_init_q(const Params &p, const Storage &sto, int q, const float *phi0, cudaStream_t st) {
-    if (q == 19)
+    if (q == 9)
+        init_kernel<T, 9, QP><<<grid1d(p.N), 256, 0, st>>>(p.N, phi0, h_view<T>(p, sto), g_view<T>(p, sto));
+    else if (q == 19)
         init_kernel<T, 19, QP><<<grid1d(p.N), 256, 0, st>>>(p.N, phi0, h_view<T>(p, sto), g_view<T>(p, sto));
     else if (q == 27)
         init_kernel<T, 27, QP><<<grid1d(p.N), 256, 0, st>>>(p.N, phi0, h_view<T>(p, sto), g_view<T>(p, sto));
@@ -69,6 +71,7 @@ static cudaError_t launch_init_q(const Params &p, const Storage &sto, int q, con
 cudaError_t launch_init(const Params &p, const Storage &sto, int q, int q_phase, const float *phi0, cudaStream_t st) {
     if (q_phase != 15) {  // the other phase lattices run with FP32 storage
         if (sto.precision != LBM_PRECISION_FP32) return cudaErrorInvalidValue;
+        if (q_phase == 9) return launch_init_q<float, 9>(p, sto, q, phi0, st);
         if (q_phase == 19) return launch_init_q<float, 19>(p, sto, q, phi0, st);
         if (q_phase == 27) return launch_init_q<float, 27>(p, sto, q, phi0, st);
         return cudaErrorInvalidValue;
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(256) fields_kernel(Params p, LatView<T> g, con
     float gv[QG];
     load_g<T, QG, G_SW>(p, g, C, gv);
     Hydro<QG> H;
-    hydro_macro<QG>(p, gv, nb[13], stencil_sums(nb), H);
+    hydro_macro<QG>(p, gv, nb[13], stencil_sums<QG == 9>(nb), H);
     if (out_phi) out_phi[C.c] = nb[13];
     if (ux) ux[C.c] = H.ux;
     if (uy) uy[C.c] = H.uy;
@@ -118,7 +121,11 @@ cudaError_t launch_fields(const Params &p, const Storage &sto, int q, bool gsw, 
     const dim3 b(32, 8, 1), gr = grid3d(p);
     LBM_BY_PRECISION(sto, {
         const LatView<T> g = g_view<T>(p, sto);
-        if (q == 19 && gsw)
+        if (q == 9 && gsw)
+            fields_kernel<T, 9, true><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
+        else if (q == 9)
+            fields_kernel<T, 9, false><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
+        else if (q == 19 && gsw)
             fields_kernel<T, 19, true><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
         else if (q == 19)
             fields_kernel<T, 19, false><<<gr, b, 0, st>>>(p, g, phi, out_phi, ux, uy, uz, pr);
@@ -186,6 +193,8 @@ static cudaError_t transfer(const Params &p, const Storage &sto, bool is_h, int 
         const LatView<T> A = is_h ? h_view<T>(p, sto) : g_view<T>(p, sto);
         if (q == 15)
             transfer_q<T, 15>(p, A, gather, sw, i0, i1, buf, st);
+        else if (q == 9)
+            transfer_q<T, 9>(p, A, gather, sw, i0, i1, buf, st);
         else if (q == 19)
             transfer_q<T, 19>(p, A, gather, sw, i0, i1, buf, st);
         else if (q == 27)
@@ -241,7 +250,7 @@ __global__ void __launch_bounds__(256) reduce_partial_kernel(Params p, LatView<T
         float gv[QG];
         load_g<T, QG, G_SW>(p, g, C, gv);
         Hydro<QG> H;
-        hydro_macro<QG>(p, gv, nb[13], stencil_sums(nb), H);
+        hydro_macro<QG>(p, gv, nb[13], stencil_sums<QG == 9>(nb), H);
         // bubble indicator: 1 in the light phase, 0 wherever phi >= 1/2
         const double f = nb[13], lf = fmin(fmax(1.0 - 2.0 * f, 0.0), 1.0), rho = H.rho;
         acc[0] += f;
@@ -300,7 +309,11 @@ cudaError_t launch_reduce(const Params &p, const Storage &sto, int q, bool gsw, 
                           double *out, cudaStream_t st) {
     LBM_BY_PRECISION(sto, {
         const LatView<T> g = g_view<T>(p, sto);
-        if (q == 19 && gsw)
+        if (q == 9 && gsw)
+            reduce_partial_kernel<T, 9, true><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);
+        else if (q == 9)
+            reduce_partial_kernel<T, 9, false><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);
+        else if (q == 19 && gsw)
             reduce_partial_kernel<T, 19, true><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);
         else if (q == 19)
             reduce_partial_kernel<T, 19, false><<<kReduceBlocks, 256, 0, st>>>(p, g, phi, scratch);

@@ -61,10 +61,11 @@ __host__ __device__ constexpr V3 vel27(int i) {
     }
 }
 
-// D3Q15 = rest, six faces, eight corners; D3Q19 = first 19 of D3Q27.
+// D3Q15 = rest, six faces, eight corners; D3Q19 = first 19 of D3Q27; D2Q9 = rest,
+// the four x, y faces and the four xy edges (the two-dimensional pair).
 template <int Q>
 __host__ __device__ constexpr V3 vel(int i) {
-    return (Q == 15 && i >= 7) ? vel27(i + 12) : vel27(i);
+    return (Q == 15 && i >= 7) ? vel27(i + 12) : (Q == 9 && i >= 5) ? vel27(i + 2) : vel27(i);
 }
 
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
@@ -74,6 +75,7 @@ template <int Q>
 __host__ __device__ constexpr float wgt(int i) {
     const V3 e = vel<Q>(i);
     const int e2 = e.x * e.x + e.y * e.y + e.z * e.z;
+    if (Q == 9) return e2 == 0 ? 4.0f / 9.0f : (e2 == 1 ? 1.0f / 9.0f : 1.0f / 36.0f);
     if (Q == 15) return e2 == 0 ? 2.0f / 9.0f : (e2 == 1 ? 1.0f / 9.0f : 1.0f / 72.0f);
     if (Q == 19) return e2 == 0 ? 1.0f / 3.0f : (e2 == 1 ? 1.0f / 18.0f : 1.0f / 36.0f);
     return e2 == 0 ? 8.0f / 27.0f : (e2 == 1 ? 2.0f / 27.0f : (e2 == 2 ? 1.0f / 54.0f : 1.0f / 216.0f));
@@ -253,6 +255,8 @@ struct Stencil {
     float L1, L2, L3;           // sum over the class of d(e) + d(-e)
 };
 
+// PLANE: the in-plane neighbours only (the D2Q9 pair on an nx x ny x 1 box).
+template <bool PLANE = false>
 __device__ __forceinline__ Stencil stencil_sums(const float nb[27]) {
     Stencil S;
 #pragma unroll
@@ -262,6 +266,7 @@ __device__ __forceinline__ Stencil stencil_sums(const float nb[27]) {
 #pragma unroll
     for (int i = 1; i < 27; i += 2) {  // i + 1 is the opposite of i
         const V3 e = vel27(i);
+        if (PLANE && e.z != 0) continue;
         const float vp = nb_at<27>(nb, i), vm = nb_at<27>(nb, i + 1);
         const float D = vp - vm, L = (vp - c) + (vm - c);
         const int cls = e.x * e.x + e.y * e.y + e.z * e.z;
@@ -279,7 +284,8 @@ __device__ __forceinline__ Stencil stencil_sums(const float nb[27]) {
 // weight of a class (|e|^2 = 1, 2, 3) in lattice Q; 0 if the class is absent
 template <int Q>
 __host__ __device__ constexpr float wclass(int cls) {
-    return Q == 15 ? (cls == 1 ? 1.0f / 9.0f : (cls == 3 ? 1.0f / 72.0f : 0.0f))
+    return Q == 9    ? (cls == 1 ? 1.0f / 9.0f : (cls == 2 ? 1.0f / 36.0f : 0.0f))
+         : Q == 15 ? (cls == 1 ? 1.0f / 9.0f : (cls == 3 ? 1.0f / 72.0f : 0.0f))
          : Q == 19 ? (cls == 1 ? 1.0f / 18.0f : (cls == 2 ? 1.0f / 36.0f : 0.0f))
                    : (cls == 1 ? 2.0f / 27.0f : (cls == 2 ? 1.0f / 54.0f : 1.0f / 216.0f));
 }
@@ -352,7 +358,8 @@ __device__ __forceinline__ void hydro_macro(const Params &p, const float gv[QG],
     // non-equilibrium second moments with u' (all forces but F_mu)
     const float upx = jx + f0x * hir, upy = jy + f0y * hir, upz = jz + f0z * hir;
     const float c3 = ps * (1.0f / 3.0f);
-    const float a2xx = mxx - c3, a2yy = myy - c3, a2zz = mzz - c3;
+    // Hermite second moments over the lattice's own dimensions (no zz for D2Q9)
+    const float a2xx = mxx - c3, a2yy = myy - c3, a2zz = QG == 9 ? 0.0f : mzz - c3;
     const float pxx = a2xx - upx * upx, pyy = a2yy - upy * upy, pzz = a2zz - upz * upz;
     const float pxy = mxy - upx * upy, pxz = mxz - upx * upz, pyz = myz - upy * upz;
     // eq:viscousForce: F_mu = -(nu / c_s^2) s_nu Pi_neq . grad rho = -tau s_nu Pi_neq . grad rho

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kNoAllocThreads) noalloc_partial_kernel(Params
 #pragma unroll
         for (int i = 0; i < QG; ++i) gv[i] = g[pop_src<QG, false>(C, p.N, i)];
         Hydro<QG> H;
-        hydro_macro<QG>(p, gv, nb[13], stencil_sums(nb), H);
+        hydro_macro<QG>(p, gv, nb[13], stencil_sums<QG == 9>(nb), H);
         // bubble indicator: 1 in the light phase, 0 wherever phi >= 1/2
         const double f = nb[13], lf = fmin(fmax(1.0 - 2.0 * f, 0.0), 1.0), rho = H.rho;
         acc[0] += f;
@@ -169,7 +169,9 @@ lbm_status lbm_reduce_state_noalloc(const lbm_domain *dom, const lbm_params *prm
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int nblocks = (int)((p.N + kNoAllocCellsPerBlock - 1) / kNoAllocCellsPerBlock);
     double *result = scratch + (size_t)kNoAllocMaxBlocks * kDiagSlots;
-    if (dom->q_hydro == 19)
+    if (dom->q_hydro == 9)
+        noalloc_partial_kernel<9><<<nblocks, kNoAllocThreads, 0, s>>>(p, g, phi, scratch);
+    else if (dom->q_hydro == 19)
         noalloc_partial_kernel<19><<<nblocks, kNoAllocThreads, 0, s>>>(p, g, phi, scratch);
     else
         noalloc_partial_kernel<27><<<nblocks, kNoAllocThreads, 0, s>>>(p, g, phi, scratch);

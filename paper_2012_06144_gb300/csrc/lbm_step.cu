@@ -39,24 +39,32 @@ constexpr int TY = LBM_TY, TZ = LBM_TZ;
 template <int QG, int QP>
 constexpr int min_blocks() { return QG + QP >= 46 ? 3 : LBM_MIN_BLOCKS; }
 
+// Tile height and depth: 32 x TY x TZ, or 32 x 8 x 1 for the D2Q9 pair (one plane).
+template <int QP>
+constexpr int tile_y() { return QP == 9 ? 8 : TY; }
+template <int QP>
+constexpr int tile_z() { return QP == 9 ? 1 : TZ; }
+
 template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT>
-__global__ void __launch_bounds__(TX *TY *TZ, min_blocks<QG, QP>())
+__global__ void __launch_bounds__(TX *tile_y<QP>() * tile_z<QP>(), min_blocks<QG, QP>())
     fused_step_kernel(Params p, Planes pl, const float *__restrict__ phi_in, float *__restrict__ phi_out,
                       int *__restrict__ flag) {
-    __shared__ float tile[TZ + 2][TY + 2][TX + 2];
+    constexpr int TYk = tile_y<QP>(), TZk = tile_z<QP>();
+    __shared__ float tile[TZk + 2][TYk + 2][TX + 2];
     // blockIdx.x runs over the (x, y) tiles, x fastest; blockIdx.y over z
     const int nbx = (p.nx + TX - 1) / TX;
     const int by = blockIdx.x / nbx, bx = blockIdx.x - by * nbx;
-    tile_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, TY, TZ>(p, TableLat{pl.h}, TableLat{pl.g}, phi_in, phi_out,
-                                                            flag, tile, bx, by, blockIdx.y, threadIdx.x,
-                                                            threadIdx.y, threadIdx.z);
+    tile_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, TYk, TZk>(p, TableLat{pl.h}, TableLat{pl.g}, phi_in, phi_out,
+                                                              flag, tile, bx, by, blockIdx.y, threadIdx.x,
+                                                              threadIdx.y, threadIdx.z);
 }
 
 template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT>
 static cudaError_t launch(const Params &p, const Planes &pl, const float *pi, float *po, int *flag,
                           cudaStream_t st) {
-    const dim3 block(TX, TY, TZ);
-    const dim3 grid(((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY), (p.nz + TZ - 1) / TZ);
+    constexpr int TYk = tile_y<QP>(), TZk = tile_z<QP>();
+    const dim3 block(TX, TYk, TZk);
+    const dim3 grid(((p.nx + TX - 1) / TX) * ((p.ny + TYk - 1) / TYk), (p.nz + TZk - 1) / TZk);
     fused_step_kernel<T, QG, QP, G_SW, H_SW, HYDRO, PMRT><<<grid, block, 0, st>>>(p, pl, pi, po, flag);
     return cudaGetLastError();
 }
@@ -72,13 +80,19 @@ static cudaError_t launch_layouts(const Params &p, const Planes &pl, int q_hydro
         return launch<T, 19, QP, false, false, false, PMRT>(p, pl, phi_in, phi_out, flag, st);
     }
     if (g_sw == h_sw) return cudaErrorInvalidValue;
-    if (q_hydro == 19)
-        return g_sw ? launch<T, 19, QP, true, false, true, PMRT>(p, pl, phi_in, phi_out, flag, st)
-                    : launch<T, 19, QP, false, true, true, PMRT>(p, pl, phi_in, phi_out, flag, st);
-    if (q_hydro == 27)
-        return g_sw ? launch<T, 27, QP, true, false, true, PMRT>(p, pl, phi_in, phi_out, flag, st)
-                    : launch<T, 27, QP, false, true, true, PMRT>(p, pl, phi_in, phi_out, flag, st);
-    return cudaErrorInvalidValue;
+    if constexpr (QP == 9) {  // the two-dimensional pair: D2Q9 for both lattices
+        if (q_hydro != 9) return cudaErrorInvalidValue;
+        return g_sw ? launch<T, 9, 9, true, false, true, PMRT>(p, pl, phi_in, phi_out, flag, st)
+                    : launch<T, 9, 9, false, true, true, PMRT>(p, pl, phi_in, phi_out, flag, st);
+    } else {
+        if (q_hydro == 19)
+            return g_sw ? launch<T, 19, QP, true, false, true, PMRT>(p, pl, phi_in, phi_out, flag, st)
+                        : launch<T, 19, QP, false, true, true, PMRT>(p, pl, phi_in, phi_out, flag, st);
+        if (q_hydro == 27)
+            return g_sw ? launch<T, 27, QP, true, false, true, PMRT>(p, pl, phi_in, phi_out, flag, st)
+                        : launch<T, 27, QP, false, true, true, PMRT>(p, pl, phi_in, phi_out, flag, st);
+        return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T>
@@ -100,6 +114,8 @@ cudaError_t launch_step(const Params &p, const Storage &sto, int q_hydro, int q_
         if (p.phase_mrt && q_phase == 15)
             return launch_layouts<float, 15, true>(p, pl, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
         if (p.phase_mrt) return cudaErrorInvalidValue;
+        if (q_phase == 9)
+            return launch_layouts<float, 9, false>(p, pl, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
         if (q_phase == 19)
             return launch_layouts<float, 19, false>(p, pl, q_hydro, g_sw, h_sw, hydro, phi_in, phi_out, flag, st);
         if (q_phase == 27)

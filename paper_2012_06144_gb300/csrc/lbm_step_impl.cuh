@@ -192,7 +192,7 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh,
                                                   int *__restrict__ flag) {
     const Codec<T> ch{p.h_ref, 1.0f, 1.0f}, cg{0.0f, p.g_scale, p.g_inv_scale};
     const float phic = nb[13];
-    const Stencil S = stencil_sums(nb);
+    const Stencil S = stencil_sums<QP == 9>(nb);
     float ux = 0.f, uy = 0.f, uz = 0.f;
 
     // ---- hydrodynamic step k-1 (Section 3.2)
@@ -313,12 +313,14 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
                                             float *__restrict__ phi_out, int *__restrict__ flag, int bx, int by,
                                             int bz, int tx, int ty, int tz) {
     constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
+    // the D2Q9 pair (nx x ny x 1 box): only the cell's own plane, kept as tile[1]
+    constexpr bool PLANE = QP == 9;
 
     // ---- phi^{k-1} tile with a one-cell halo (wrap on periodic axes, mirror at
     // walls), filled row by row: warp w loads rows w, w + 8, ... of the HZ x HY
     // rows, lane l the x-offsets l and (lanes 0, 1) 32 + l.  The loads are issued
     // before the population loads so that their latency overlaps.
-    constexpr int NROW = HY * HZ, NWARP = TX * TY * TZ / 32, RPW = (NROW + NWARP - 1) / NWARP;
+    constexpr int NROW = PLANE ? HY : HY * HZ, NWARP = TX * TY * TZ / 32, RPW = (NROW + NWARP - 1) / NWARP;
     const int lane = tx, warp = ty + TY * tz;
     const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
     const int gx0 = min(wrap_or_clamp(bx * TX - 1 + lane, p.nx, wx), p.nx - 1);
@@ -328,11 +330,11 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
     for (int k = 0; k < RPW; ++k) {
         const int r = warp + k * NWARP;
         if (r < NROW) {
-            const int kz = r / HY, ky = r - kz * HY;
+            const int kz = PLANE ? 1 : r / HY, ky = PLANE ? r : r - kz * HY;
             // coordinates beyond a ragged box end are clamped into the box; those
             // halo entries only feed threads that are inactive
             const int gy = min(wrap_or_clamp(by * TY - 1 + ky, p.ny, wy), p.ny - 1);
-            const int gz = min(wrap_or_clamp(bz * TZ - 1 + kz, p.nz, wz), p.nz - 1);
+            const int gz = PLANE ? bz : min(wrap_or_clamp(bz * TZ - 1 + kz, p.nz, wz), p.nz - 1);
             const float *row = phi_in + (size_t)gy * p.nx + (size_t)gz * p.nx * p.ny;
             tv0[k] = __ldg(row + gx0);
             if (lane < HX - 32) tv1[k] = __ldg(row + gx1);
@@ -355,7 +357,7 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
     for (int k = 0; k < RPW; ++k) {
         const int r = warp + k * NWARP;
         if (r < NROW) {
-            const int kz = r / HY, ky = r - kz * HY;
+            const int kz = PLANE ? 1 : r / HY, ky = PLANE ? r : r - kz * HY;
             tile[kz][ky][lane] = tv0[k];
             if (lane < HX - 32) tile[kz][ky][32 + lane] = tv1[k];
         }
@@ -369,7 +371,7 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
         for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx)
-                nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
+                nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[PLANE ? 1 : tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
     collide_and_store<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, EDGE>(p, lh, lg, n, gv, hv, nb, phi_out, flag);
 }
 

@@ -227,3 +227,21 @@ def test_other_phase_lattices_limits(lbm):
         with pytest.raises(lbm.LBMError) as ei:
             lbm.lbm_batch_create([d], [lbm.make_params()])
         assert ei.value.status == lbm.LBM_ERR_ARG
+
+
+def test_d2q9_pair_limits(lbm):
+    p = lbm.make_params()
+    ok = lbm.make_domain(64, 32, 1, q_hydro=9, q_phase=9)
+    assert lbm.lbm_workspace_size(ok, p) >= (9 + 9 + 2) * 64 * 32 * 4
+    bad = [lbm.make_domain(64, 32, 2, q_hydro=9, q_phase=9),          # nz must be 1
+           lbm.make_domain(64, 32, 1, q_hydro=19, q_phase=9),         # a pair
+           lbm.make_domain(64, 32, 1, q_hydro=9, q_phase=15),
+           lbm.make_domain(64, 32, 1, wall=(0, 0, 1), q_hydro=9, q_phase=9)]
+    for d in bad:
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_workspace_size(d, p)
+        assert ei.value.status == lbm.LBM_ERR_ARG
+    for prm in (lbm.make_params(gravity=(0.0, 0.0, 1e-5)), lbm.make_params(precision=lbm.LBM_PRECISION_FP16)):
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_workspace_size(ok, prm)
+        assert ei.value.status == lbm.LBM_ERR_ARG

@@ -22,6 +22,10 @@ Workloads (cell centres at i + 1/2, y is "up"):
   buoyancy reference = mean density (periodic gravity axis).
 * ``precision_bubble`` 64^3 walled rising bubble, D = 16 at (32, 16, 32),
   Eo = 10, Mo = 1e-3, t_ref = 1000.
+* ``batched``          64 walled rising bubbles of four box sizes, seeded draws of
+  density ratio and Eo (batched stepping).
+* ``roofline2d``       8192 x 16384 x 1 periodic, D2Q9 + D2Q9, light circles on a
+  square lattice, the roofline physics (the two-dimensional pair).
 """
 from __future__ import annotations
 
@@ -43,7 +47,7 @@ class Problem:
     nz: int
     wall: tuple = (0, 0, 0)  # 0 = periodic axis, 1 = no-slip walls on both faces
     q_hydro: int = 27
-    q_phase: int = 15  # phase-field lattice: 15 (the benchmarked pair), 19 or 27
+    q_phase: int = 15  # phase-field lattice: 15 (the benchmarked pair), 19, 27; 9 with q_hydro 9 (2-D)
     rho_H: float = 1.0
     rho_ratio: float = 1000.0
     nu_H: float = 0.01
@@ -260,6 +264,25 @@ def batched(count: int = 64, seed: int = SEED, u_s: float = 0.016, re_gr: float 
         phi0 = sphere_phi(prob, (nx / 2, 2 * D, nz / 2), D / 2, heavy_inside=False).astype(np.float32)
         out.append((prob, phi0, dict(size=size, rho_ratio=ratio, Eo=Eo, D=D)))
     return out
+
+
+def roofline2d(nx: int = 8192, ny: int = 16384, radius: float = 12.0, spacing: int = 64):
+    """The two-dimensional pair's benchmark box (nx x ny x 1, D2Q9 for both
+    lattices, triply periodic): light circles of radius 12 on a square lattice of
+    pitch 64 in heavy fluid, the roofline workload's physics (density ratio 1000,
+    viscosity ratio 100, sigma 1e-4, xi 5, M 0.02, gravity from Eo 10 at D 24,
+    rho_ref the mean density).  134.2 M cells at the default size, as 512^3."""
+    sigma, Eo, D_ref = 1e-4, 10.0, 24.0
+    g = Eo * sigma / (D_ref * D_ref)
+    prob = Problem(nx, ny, 1, wall=(0, 0, 0), q_hydro=9, q_phase=9, rho_H=1.0, rho_ratio=1000.0, nu_H=0.01,
+                   mu_ratio=100.0, sigma=sigma, xi=5.0, mobility=0.02, gravity=(0.0, -g, 0.0), clamp_phi=1)
+    x = (np.arange(nx) + 0.5) % spacing - spacing / 2
+    y = (np.arange(ny) + 0.5) % spacing - spacing / 2
+    r = np.sqrt(y[:, None] ** 2 + x[None, :] ** 2).astype(np.float32)
+    phi0 = (0.5 - 0.5 * np.tanh(2.0 * (radius - r) / prob.xi)).astype(np.float32)[None]
+    mean_phi = float(phi0.astype(np.float64).mean())
+    prob.rho_ref = prob.rho_L + mean_phi * (prob.rho_H - prob.rho_L)
+    return prob, phi0
 
 
 def roofline(n: int = 512, count: int = 400, dmin: float = 16.0, dmax: float = 32.0, seed: int = SEED):
