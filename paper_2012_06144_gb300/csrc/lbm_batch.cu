@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
     __shared__ float tile[TZ + 2][TY + 2][TX + 2];
     const int4 e = tiles[blockIdx.x];
     const MemberDesc &d = a.m[e.x];
-    tile_update<float, QG, 15, G_SW, H_SW, true, false, TY, TZ>(d.p, TableLat{d.h}, TableLat{d.g}, d.phi[cur],
+    tile_update<float, QG, 15, G_SW, H_SW, true, false, TY, TZ, true>(d.p, TableLat{d.h}, TableLat{d.g}, d.phi[cur],
                                                             d.phi[cur ^ 1], d.flag, tile, e.y, e.z, e.w,
                                                             threadIdx.x, threadIdx.y, threadIdx.z);
 }

@@ -78,10 +78,15 @@ __device__ __forceinline__ int nidx(const Nb3 &n, int dx, int dy, int dz) {
     return n.X[dx + 1] + n.Y[dy + 1] + n.Z[dz + 1];
 }
 
+// True if x + sign e leaves the box through a wall on one of the axes in AXES
+// (bit a: axis a); the tile knows which walled faces it can touch.
+template <int AXES>
 __device__ __forceinline__ bool leaves3(const Nb3 &n, V3 e, int sign) {
     const int ex = e.x * sign, ey = e.y * sign, ez = e.z * sign;
-    return (ex > 0 && (n.hi & 1)) || (ex < 0 && (n.lo & 1)) || (ey > 0 && (n.hi & 2)) || (ey < 0 && (n.lo & 2)) ||
-           (ez > 0 && (n.hi & 4)) || (ez < 0 && (n.lo & 4));
+    if constexpr (AXES == 1) return (ex > 0 && (n.hi & 1)) || (ex < 0 && (n.lo & 1));
+    else
+        return (ex > 0 && (n.hi & 1)) || (ex < 0 && (n.lo & 1)) || (ey > 0 && (n.hi & 2)) || (ey < 0 && (n.lo & 2)) ||
+               (ez > 0 && (n.hi & 4)) || (ez < 0 && (n.lo & 4));
 }
 
 template <typename T>
@@ -124,7 +129,7 @@ struct Codec {
 };
 
 // (slot, element) holding the pre-collision f_i(x) in the AA layout (see lbm_device.cuh)
-template <int Q, bool SW, bool EDGE>
+template <int Q, bool SW, int EDGE>
 __device__ __forceinline__ void src_loc(const Nb3 &n, int i, int &slot, int &idx) {
     if (!SW) {
         slot = i;
@@ -132,7 +137,7 @@ __device__ __forceinline__ void src_loc(const Nb3 &n, int i, int &slot, int &idx
         return;
     }
     const V3 e = vel<Q>(i);
-    if (EDGE && leaves3(n, e, -1)) {
+    if (EDGE && leaves3<EDGE>(n, e, -1)) {
         slot = i;
         idx = n.X[1];
         return;
@@ -142,7 +147,7 @@ __device__ __forceinline__ void src_loc(const Nb3 &n, int i, int &slot, int &idx
 }
 
 // (slot, element) that receives the post-collision f*_i(x)
-template <int Q, bool SW, bool EDGE>
+template <int Q, bool SW, int EDGE>
 __device__ __forceinline__ void dst_loc(const Nb3 &n, int i, int &slot, int &idx) {
     if (!SW) {
         slot = opp(i);
@@ -150,7 +155,7 @@ __device__ __forceinline__ void dst_loc(const Nb3 &n, int i, int &slot, int &idx
         return;
     }
     const V3 e = vel<Q>(i);
-    if (EDGE && leaves3(n, e, +1)) {
+    if (EDGE && leaves3<EDGE>(n, e, +1)) {
         slot = opp(i);
         idx = n.X[1];
         return;
@@ -159,7 +164,7 @@ __device__ __forceinline__ void dst_loc(const Nb3 &n, int i, int &slot, int &idx
     idx = nidx(n, e.x, e.y, e.z);
 }
 
-template <typename T, int Q, bool SW, bool EDGE, typename L>
+template <typename T, int Q, bool SW, int EDGE, typename L>
 __device__ __forceinline__ float pop_load(const L &lat, const Nb3 &n, int i, const Codec<T> &cd) {
     int slot, idx;
     src_loc<Q, SW, EDGE>(n, i, slot, idx);
@@ -168,14 +173,14 @@ __device__ __forceinline__ float pop_load(const L &lat, const Nb3 &n, int i, con
 }
 
 // stores the rest population (i = 0, FP32) or an encoded moving population
-template <typename T, int Q, bool SW, bool EDGE, typename L>
+template <typename T, int Q, bool SW, int EDGE, typename L>
 __device__ __forceinline__ void pop_store_rest(const L &lat, const Nb3 &n, float v) {
     int slot, idx;
     dst_loc<Q, SW, EDGE>(n, 0, slot, idx);
     st_pop(lat.template ptr<float>(0) + idx, v);
 }
 
-template <typename T, int Q, bool SW, bool EDGE, typename L>
+template <typename T, int Q, bool SW, int EDGE, typename L>
 __device__ __forceinline__ void pop_store_enc(const L &lat, const Nb3 &n, int i, T q) {
     int slot, idx;
     dst_loc<Q, SW, EDGE>(n, i, slot, idx);
@@ -185,7 +190,7 @@ __device__ __forceinline__ void pop_store_enc(const L &lat, const Nb3 &n, int i,
 // Collision of both lattices at one cell and the streaming stores, from the
 // pre-collision populations gv (g^{k-1}), hv (h^k) and the 3x3x3 neighbourhood nb
 // of phi^{k-1}.
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, bool EDGE, typename LH,
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, int EDGE, typename LH,
           typename LG>
 __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh, const LG &lg, const Nb3 &n, const float *gv,
                                                   const float *hv, const float *nb, float *__restrict__ phi_out,
@@ -306,7 +311,7 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh,
     pop_store_rest<T, QP, H_SW, EDGE>(lh, n, hv[0] - dsum);
 }
 
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, bool EDGE, int TY, int TZ,
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, int EDGE, int TY, int TZ,
           typename LH, typename LG>
 __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const LG &lg, const Nb3 &n, bool active,
                                             const float *__restrict__ phi_in, float (*tile)[TY + 2][TX + 2],
@@ -378,8 +383,11 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
 // One tile (bx, by, bz) of 32 x TY x TZ cells, one thread per cell: per-thread
 // neighbour offsets, then the bounce-back-checking path only if the tile touches
 // a walled face.  Every thread of the block must call this (it synchronises).
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, int TY, int TZ, typename LH,
-          typename LG>
+// XONLY: a tile that touches only the x walls takes a path that tests the x walls
+// alone (the batched walled boxes, at most 64 cells wide, are mostly such tiles;
+// for the single-simulation kernel the extra path cost more than it saved).
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, int TY, int TZ, bool XONLY = false,
+          typename LH, typename LG>
 __device__ __forceinline__ void tile_update(const Params &p, const LH &lh, const LG &lg,
                                             const float *__restrict__ phi_in, float *__restrict__ phi_out,
                                             int *__restrict__ flag, float (*tile)[TY + 2][TX + 2], int bx, int by,
@@ -406,14 +414,19 @@ __device__ __forceinline__ void tile_update(const Params &p, const LH &lh, const
     n.lo = (wx && xc == 0 ? 1 : 0) | (wy && yc == 0 ? 2 : 0) | (wz && zc == 0 ? 4 : 0);
     n.hi = (wx && xc == p.nx - 1 ? 1 : 0) | (wy && yc == p.ny - 1 ? 2 : 0) | (wz && zc == p.nz - 1 ? 4 : 0);
 
-    const bool edge = (wx && (bx == 0 || (bx + 1) * TX >= p.nx)) || (wy && (by == 0 || (by + 1) * TY >= p.ny)) ||
-                      (wz && (bz == 0 || (bz + 1) * TZ >= p.nz));
-    if (edge)
-        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, true, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
-                                                            by, bz, tx, ty, tz);
+    // the walled faces this tile touches, by axis: none (the plain path), the x walls
+    // only (every tile of a walled box at most 64 cells wide), or any
+    const bool ex = wx && (bx == 0 || (bx + 1) * TX >= p.nx), ey = wy && (by == 0 || (by + 1) * TY >= p.ny),
+               ez = wz && (bz == 0 || (bz + 1) * TZ >= p.nz);
+    if (!(ex || ey || ez))
+        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, 0, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag,
+                                                                   bx, by, bz, tx, ty, tz);
+    else if (XONLY && !(ey || ez))
+        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, 1, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag,
+                                                                   bx, by, bz, tx, ty, tz);
     else
-        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, false, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
-                                                             by, bz, tx, ty, tz);
+        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, 7, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag,
+                                                                   bx, by, bz, tx, ty, tz);
 }
 
 }  // namespace lbm
