@@ -67,6 +67,8 @@ def _pins(orc):
         P.append(lambda q=q: I.test_lattice_moments(orc, q))
         P.append(lambda q=q: I.test_stencils_exact_on_quadratics(orc, q))
     P += [
+        lambda: D.test_d2q9_lattice_moments(orc),
+        lambda: D.test_d2q9_hydro_collision_moments(orc),
         lambda: I.test_stencil_walls_mirror(orc),
         lambda: I.test_phase_collision_moments(orc, 15),
         lambda: I.test_phase_normal_zero_gradient(orc, 15),
@@ -88,8 +90,6 @@ def _pins(orc):
         lambda: Ph.test_two_layer_poiseuille_diffuse(orc, 10.0, 1.0, 0.05, 8.0, 19, 1.5e-2),
         lambda: Ph.test_two_layer_poiseuille_diffuse(orc, 1000.0, 100.0, 0.05, 4.0, 27, 1e-2),
         lambda: Ph.test_laplace_law_cylinder(orc),
-        lambda: D.test_d2q9_lattice_moments(orc),
-        lambda: D.test_d2q9_hydro_collision_moments(orc),
         lambda: D.test_d2q9_shear_wave_viscosity(orc),
     ]
     return P
