@@ -87,7 +87,10 @@ enum { LBM_FORM_FUSED = 0, LBM_FORM_UNFUSED = 1 };
 /* Box and lattices (Section 3; Section 5 uses D3Q15 for h and D3Q27 for g). */
 typedef struct {
     int nx, ny, nz; /* cells per axis, each >= 1, nx*ny*nz < 2^31,
-                       ny <= 524280, nz <= 65535 (launch-grid limits)       */
+                       ny <= 524280, nz <= 65535 (launch-grid limits); boxes
+                       with (max(q_phase, q_hydro) - 1) nx ny nz >= 2^32 (about
+                       165 M cells at D3Q27) need FP32 storage, the SRT phase
+                       collision and the D3Q15 phase lattice                   */
     int wall[3];    /* 0 = periodic axis, 1 = no-slip walls on both faces       */
     int q_phase;    /* 15 (the benchmarked pair), 19 or 27; 19 and 27 need FP32
                        storage, the SRT phase collision and the fused form      */

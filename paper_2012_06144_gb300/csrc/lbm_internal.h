@@ -33,6 +33,14 @@ struct Unfused {
 cudaError_t launch_unfused(const Params &p, const Unfused &uf, const Storage &sto, int q_hydro, bool hydro,
                            const float *phi_in, float *phi_out, int *flag, cudaStream_t st);
 
+// True if every moving-plane element offset (q - 1) N of both lattices fits 32
+// bits (the fused kernel's default addressing; larger boxes take 64-bit plane
+// pointers, with FP32 storage, the SRT phase collision and the D3Q15 phase lattice).
+inline bool offsets32(long long N, int q_hydro, int q_phase) {
+    const int q = q_hydro > q_phase ? q_hydro : q_phase;
+    return (unsigned long long)N * (unsigned long long)(q - 1) < (1ull << 32);
+}
+
 // One launch of the fused kernel K_k = hydro(k-1) + phase(k) (hydro = true), or
 // the first phase step alone (hydro = false).  g_swapped / h_swapped give the
 // current AA layout of each lattice.

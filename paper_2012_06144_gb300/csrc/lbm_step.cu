@@ -49,7 +49,10 @@ constexpr int tile_y() { return QP == 9 ? LBM_TY2D : TY; }
 template <int QP>
 constexpr int tile_z() { return QP == 9 ? 1 : TZ; }
 
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT>
+// L32: population addresses as each lattice's moving-plane base plus a 32-bit
+// element offset (s - 1) N + idx (boxes with (q - 1) N < 2^32); otherwise one
+// 64-bit base pointer per plane from the kernel parameters.
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, bool L32>
 __global__ void __launch_bounds__(TX *tile_y<QP>() * tile_z<QP>(), min_blocks<QG, QP>())
     fused_step_kernel(Params p, Planes pl, const float *__restrict__ phi_in, float *__restrict__ phi_out,
                       int *__restrict__ flag) {
@@ -58,20 +61,59 @@ __global__ void __launch_bounds__(TX *tile_y<QP>() * tile_z<QP>(), min_blocks<QG
     // blockIdx.x runs over the (x, y) tiles, x fastest; blockIdx.y over z
     const int nbx = (p.nx + TX - 1) / TX;
     const int by = blockIdx.x / nbx, bx = blockIdx.x - by * nbx;
-    tile_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, TYk, TZk>(p, TableLat{pl.h}, TableLat{pl.g}, phi_in, phi_out,
-                                                              flag, tile, bx, by, blockIdx.y, threadIdx.x,
-                                                              threadIdx.y, threadIdx.z);
+    if constexpr (L32) {
+        const BaseLat32<T> lh{static_cast<float *>(pl.h[0]), static_cast<T *>(pl.h[1]), (unsigned)p.N},
+            lg{static_cast<float *>(pl.g[0]), static_cast<T *>(pl.g[1]), (unsigned)p.N};
+        tile_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, TYk, TZk>(p, lh, lg, phi_in, phi_out, flag, tile, bx, by,
+                                                                  blockIdx.y, threadIdx.x, threadIdx.y, threadIdx.z);
+    } else {
+        tile_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, TYk, TZk>(p, TableLat{pl.h}, TableLat{pl.g}, phi_in,
+                                                                  phi_out, flag, tile, bx, by, blockIdx.y,
+                                                                  threadIdx.x, threadIdx.y, threadIdx.z);
+    }
+}
+
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, bool L32>
+static cudaError_t launch_k(const Params &p, const Planes &pl, const float *pi, float *po, int *flag,
+                            cudaStream_t st) {
+    constexpr int TYk = tile_y<QP>(), TZk = tile_z<QP>();
+    const dim3 block(TX, TYk, TZk);
+    const dim3 grid(((p.nx + TX - 1) / TX) * ((p.ny + TYk - 1) / TYk), (p.nz + TZk - 1) / TZk);
+    fused_step_kernel<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, L32><<<grid, block, 0, st>>>(p, pl, pi, po, flag);
+    return cudaGetLastError();
+}
+
+// Addressing per storage type and lattice pair, from a same-GPU comparison on the
+// benchmark boxes (32-bit offsets against per-plane pointers, MLUPS): FP32
+// D3Q15+D3Q27 +0.6 % (periodic 512^3) and +3.2 % (walled 128x512x128), FP16 +2.7 %,
+// D2Q9 +2.4 %; BF16 -0.7 %, D3Q15+D3Q19 -1.0 %, D3Q19+D3Q19 -4.0 %, D3Q27+D3Q27 0.0 %.
+#ifndef LBM_ADDR_POLICY
+#define LBM_ADDR_POLICY -1  // -1: per configuration (below); 0: pointers everywhere; 1: offsets everywhere
+#endif
+
+template <typename T, int QG, int QP>
+constexpr bool prefer_offsets32() {
+    if (LBM_ADDR_POLICY >= 0) return LBM_ADDR_POLICY == 1 && !(QG == 19 && !std::is_same<T, float>::value);
+    if (std::is_same<T, __nv_bfloat16>::value) return false;
+    if (QG == 19 || QP == 19 || QP == 27) return false;
+    return true;  // D3Q15 + D3Q27 in FP32 or FP16, and D2Q9
 }
 
 template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT>
 static cudaError_t launch(const Params &p, const Planes &pl, const float *pi, float *po, int *flag,
                           cudaStream_t st) {
-    constexpr int TYk = tile_y<QP>(), TZk = tile_z<QP>();
-    const dim3 block(TX, TYk, TZk);
-    const dim3 grid(((p.nx + TX - 1) / TX) * ((p.ny + TYk - 1) / TYk), (p.nz + TZk - 1) / TZk);
-    fused_step_kernel<T, QG, QP, G_SW, H_SW, HYDRO, PMRT><<<grid, block, 0, st>>>(p, pl, pi, po, flag);
-    return cudaGetLastError();
+    if constexpr (prefer_offsets32<T, QG, QP>()) {
+        if (offsets32(p.N, QG, QP)) return launch_k<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, true>(p, pl, pi, po, flag, st);
+        // larger boxes: the pointer form, FP32 / SRT / D3Q15 only (checked on creation)
+        if constexpr (std::is_same<T, float>::value && QP == 15 && !PMRT)
+            return launch_k<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, false>(p, pl, pi, po, flag, st);
+        else
+            return cudaErrorInvalidValue;
+    } else {
+        return launch_k<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, false>(p, pl, pi, po, flag, st);
+    }
 }
+
 
 // The layouts of one time step: g natural and h swapped, or g swapped and h
 // natural (h runs one AA step ahead); the first phase step alone (no hydro)

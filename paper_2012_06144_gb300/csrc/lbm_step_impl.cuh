@@ -51,6 +51,25 @@ struct TableLat {
     __device__ __forceinline__ U *ptr(int s) const {
         return static_cast<U *>(t[s]);
     }
+    template <typename U>
+    __device__ __forceinline__ U *at(int s, int idx) const {
+        return static_cast<U *>(t[s]) + idx;
+    }
+};
+
+// Plane addresses of one lattice from its rest plane and first moving plane,
+// with 32-bit element offsets (s - 1) N + idx into the moving planes (for boxes
+// where 26 N < 2^32).
+template <typename T>
+struct BaseLat32 {
+    float *rest;
+    T *mov;
+    unsigned N;
+    template <typename U>
+    __device__ __forceinline__ U *at(int s, int idx) const {
+        if (s == 0) return reinterpret_cast<U *>(rest) + idx;
+        return reinterpret_cast<U *>(mov) + ((unsigned)(s - 1) * N + (unsigned)idx);
+    }
 };
 
 // Plane addresses of one lattice from its rest plane and first moving plane
@@ -64,6 +83,10 @@ struct BaseLat {
     __device__ __forceinline__ U *ptr(int s) const {
         if (s == 0) return reinterpret_cast<U *>(rest);
         return reinterpret_cast<U *>(mov + (size_t)(s - 1) * N);
+    }
+    template <typename U>
+    __device__ __forceinline__ U *at(int s, int idx) const {
+        return ptr<U>(s) + idx;
     }
 };
 
@@ -168,8 +191,8 @@ template <typename T, int Q, bool SW, int EDGE, typename L>
 __device__ __forceinline__ float pop_load(const L &lat, const Nb3 &n, int i, const Codec<T> &cd) {
     int slot, idx;
     src_loc<Q, SW, EDGE>(n, i, slot, idx);
-    if (slot == 0) return ld_pop(lat.template ptr<float>(0) + idx);
-    return cd.template decode<Q>(ld_pop(lat.template ptr<T>(slot) + idx), i);
+    if (slot == 0) return ld_pop(lat.template at<float>(0, idx));
+    return cd.template decode<Q>(ld_pop(lat.template at<T>(slot, idx)), i);
 }
 
 // stores the rest population (i = 0, FP32) or an encoded moving population
@@ -177,14 +200,14 @@ template <typename T, int Q, bool SW, int EDGE, typename L>
 __device__ __forceinline__ void pop_store_rest(const L &lat, const Nb3 &n, float v) {
     int slot, idx;
     dst_loc<Q, SW, EDGE>(n, 0, slot, idx);
-    st_pop(lat.template ptr<float>(0) + idx, v);
+    st_pop(lat.template at<float>(0, idx), v);
 }
 
 template <typename T, int Q, bool SW, int EDGE, typename L>
 __device__ __forceinline__ void pop_store_enc(const L &lat, const Nb3 &n, int i, T q) {
     int slot, idx;
     dst_loc<Q, SW, EDGE>(n, i, slot, idx);
-    st_pop(lat.template ptr<T>(slot) + idx, q);
+    st_pop(lat.template at<T>(slot, idx), q);
 }
 
 // Collision of both lattices at one cell and the streaming stores, from the

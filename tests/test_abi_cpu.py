@@ -245,3 +245,16 @@ def test_d2q9_pair_limits(lbm):
         with pytest.raises(lbm.LBMError) as ei:
             lbm.lbm_workspace_size(ok, prm)
         assert ei.value.status == lbm.LBM_ERR_ARG
+
+
+def test_large_box_limits(lbm):
+    """Beyond 32-bit plane offsets only the FP32 / SRT / D3Q15-phase form runs."""
+    d = lbm.make_domain(576, 576, 544, q_hydro=27)
+    assert lbm.lbm_workspace_size(d, lbm.make_params()) > 0
+    for kw in (dict(precision=lbm.LBM_PRECISION_FP16), dict(phase_collision=lbm.LBM_PHASE_MRT)):
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_workspace_size(d, lbm.make_params(**kw))
+        assert ei.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_workspace_size(lbm.make_domain(576, 576, 544, q_hydro=27, q_phase=27), lbm.make_params())
+    assert ei.value.status == lbm.LBM_ERR_ARG

@@ -105,3 +105,32 @@ def test_roofline_512_mass_and_finiteness(lbm):
     assert d["max_u"] < 0.1
     del sim
     torch.cuda.empty_cache()
+
+
+def test_beyond_32bit_offsets_sampled_parity(lbm, orc):
+    """A box whose moving-plane offsets exceed 32 bits (26 N >= 2^32: 576 x 576 x 544,
+    180 M cells) runs the 64-bit plane-pointer form of the fused kernel; sampled
+    one-step parity in both in-place layouts, as for the 512^3 benchmark box."""
+    import torch
+
+    nx, ny, nz = 576, 576, 544
+    assert 26 * nx * ny * nz >= 2 ** 32
+    prob = W.Problem(nx, ny, nz, wall=(0, 0, 0), q_hydro=27, rho_ratio=100.0, sigma=1e-3, xi=4.0,
+                     gravity=(0.0, -1e-6, 0.0), rho_ref=0.5, clamp_phi=1)
+    two_pi = 2.0 * np.pi
+    x = torch.arange(nx, device="cuda", dtype=torch.float32) + 0.5
+    y = torch.arange(ny, device="cuda", dtype=torch.float32) + 0.5
+    z = torch.arange(nz, device="cuda", dtype=torch.float32) + 0.5
+    phi0 = (0.5 + 0.45 * torch.sin(two_pi * x / nx)[None, None, :] * torch.sin(two_pi * 3 * y / ny)[None, :, None]
+            * torch.cos(two_pi * 2 * z / nz)[:, None, None]).contiguous()
+    sim = lbm.Simulation.from_problem(prob)
+    sim.init_phase(phi0)
+    rng = np.random.default_rng(576)
+    cells = [(int(rng.integers(0, nz)), int(rng.integers(0, ny)), int(rng.integers(0, nx))) for _ in range(24)]
+    cells += [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (nz - 1, 0, nx - 1)]
+    for warm in (0, 1):
+        sim.step(warm)
+        check_sampled_step(lbm, orc, sim, prob, cells)
+    sim.synchronize()
+    del sim
+    torch.cuda.empty_cache()
