@@ -223,8 +223,10 @@ lbm_status lbm_batch_workspace_size(int count, const lbm_domain *doms, const lbm
 
 /* Creates a batch of count (1..65536) members from count domains and
  * parameter sets (validated as by lbm_create; every q_hydro equal, every
- * precision LBM_PRECISION_FP32, every phase_collision LBM_PHASE_SRT and every
- * kernel_form LBM_FORM_FUSED, else LBM_ERR_ARG) on the current CUDA device.
+ * precision LBM_PRECISION_FP32, every phase_collision LBM_PHASE_SRT, every
+ * kernel_form LBM_FORM_FUSED, every q_phase 15 and every member small enough
+ * that (q_hydro - 1) * nx * ny * nz < 2^32, else LBM_ERR_ARG) on the current
+ * CUDA device.
  * cuda_stream: stream for all of the batch's work (members included), NULL for
  * the legacy default stream (then no CUDA graphs are used).  workspace: device
  * buffer of lbm_batch_workspace_size() bytes, 256-byte aligned, owned by the

@@ -229,6 +229,19 @@ def test_other_phase_lattices_limits(lbm):
         assert ei.value.status == lbm.LBM_ERR_ARG
 
 
+
+def test_batch_member_beyond_32bit_offsets_rejected(lbm):
+    """Batch members are addressed with 32-bit plane offsets: (q_hydro - 1) * cells
+    at 2^32 or above is refused before any device allocation."""
+    big = lbm.make_domain(640, 640, 416, q_hydro=27)  # 26 * 170.4 M cells > 2^32
+    assert 26 * 640 * 640 * 416 >= 2 ** 32
+    assert lbm.lbm_workspace_size(big, lbm.make_params()) > 0  # a single simulation takes it
+    small = lbm.make_domain(8, 8, 8, q_hydro=27)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_batch_create([small, big], [lbm.make_params(), lbm.make_params()])
+    assert ei.value.status == lbm.LBM_ERR_ARG
+    assert "2^32" in str(ei.value)
+
 def test_d2q9_pair_limits(lbm):
     p = lbm.make_params()
     ok = lbm.make_domain(64, 32, 1, q_hydro=9, q_phase=9)
