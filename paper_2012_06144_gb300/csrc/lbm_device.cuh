@@ -316,7 +316,10 @@ struct Hydro {
     float rho;
 };
 
-template <int QG>
+// SCALED: gv holds the populations multiplied by p.g_scale (a power of two, the
+// 16-bit storage units); the moment sums are taken in those units and brought
+// back with one multiplication each, which is exact.
+template <int QG, bool SCALED = false>
 __device__ __forceinline__ void hydro_macro(const Params &p, const float gv[QG], float phi, const Stencil &S,
                                             Hydro<QG> &H) {
     // moments of g over opposite pairs: s = g_i + g_opp(i) carries the even
@@ -334,6 +337,19 @@ __device__ __forceinline__ void hydro_macro(const Params &p, const float gv[QG],
         if (e.x && e.y) mxy += (e.x * e.y > 0) ? s : -s;
         if (e.x && e.z) mxz += (e.x * e.z > 0) ? s : -s;
         if (e.y && e.z) myz += (e.y * e.z > 0) ? s : -s;
+    }
+    if constexpr (SCALED) {
+        const float r = p.g_inv_scale;
+        ps *= r;
+        jx *= r;
+        jy *= r;
+        jz *= r;
+        mxx *= r;
+        myy *= r;
+        mzz *= r;
+        mxy *= r;
+        mxz *= r;
+        myz *= r;
     }
     float gpx, gpy, gpz;
     stencil_grad<QG>(S, gpx, gpy, gpz);
@@ -413,6 +429,23 @@ __device__ __forceinline__ HydroPost<QG> hydro_post(const Hydro<QG> &H) {
     P.byz = 9.0f * (r * H.a2yz + s * H.uy * H.uz);
     P.tr3 = 1.5f * (bxx + byy + bzz);  // 4.5 * trace / 3
     return P;
+}
+
+// The coefficients of hydro_post multiplied by s (a power of two: exact), so that
+// hydro_gstar_pair returns s g*_i.
+template <int QG>
+__device__ __forceinline__ void scale_post(HydroPost<QG> &P, float s) {
+    P.m0 *= s;
+    P.m1x *= s;
+    P.m1y *= s;
+    P.m1z *= s;
+    P.bxx *= s;
+    P.byy *= s;
+    P.bzz *= s;
+    P.bxy *= s;
+    P.bxz *= s;
+    P.byz *= s;
+    P.tr3 *= s;
 }
 
 // Even and odd parts of g*_i for a direction i of an opposite pair:
