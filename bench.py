@@ -13,7 +13,8 @@ Prints one JSON line:
                upload of phi0, initialisation, K steps, download of phi, u, p and
                the diagnostics, all inside the timed region;
   roofline     algorithmic bytes per launch / mean launch time vs the measured HBM
-               copy bandwidth;
+               copy bandwidth, and (pattern_ceiling) vs the bandwidth the step's
+               AA streaming pattern reaches without arithmetic (pattern_probe);
   cpu_baseline the FP64 oracle on the host cores on a bounded sample.
 ``--impl reference`` times the FP64 oracle instead (the reference arm).
 """
@@ -342,6 +343,25 @@ def batched_form(args, stream, peak):
     return out
 
 
+def pattern_ceiling(size: int, achieved: float):
+    """The bandwidth of the step's data movement without its arithmetic, from the
+    stand-alone pattern_probe program: 42 FP32 planes moved under the fused
+    kernel's AA pattern (one lattice natural, the other swapped), next to a plain
+    copy and the other streaming schemes.  frac = the kernel's achieved
+    (algorithmic) GB/s over that ceiling."""
+    from paper_2012_06144_gb300 import _build
+
+    if size < 32 or size > 512 or size & (size - 1):
+        return None
+    try:
+        r = subprocess.run([_build.PROBE, str(size)], capture_output=True, text=True, timeout=300)
+        probe = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as exc:  # reported, not fatal: the ceiling is context for the roofline
+        return {"error": str(exc)[:200]}
+    return {"pattern": "AA: one lattice natural, the other swapped (42 FP32 planes, no arithmetic)",
+            "gbs": probe["aa_mix"], "frac": achieved / probe["aa_mix"], "probe": probe}
+
+
 def unfused_bytes_per_cell(q: int) -> int:
     """Algorithmic bytes of one unfused step per cell (FP32): hydro collision
     2q + 1 + 3, phase collision 15 + 15 + 1 + 3 + 1, streaming 2 x 15 and 2 x q."""
@@ -482,6 +502,7 @@ def main():
     ap.add_argument("--no-rising", action="store_true", help="skip the rising-bubble observables")
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused baseline")
     ap.add_argument("--no-pairs", action="store_true", help="skip the other stencil pairs")
+    ap.add_argument("--no-pattern", action="store_true", help="skip the streaming-pattern bandwidth ceiling")
     ap.add_argument("--rising-steps", type=int, default=10000, help="steps of the rising-bubble run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -572,6 +593,9 @@ def main():
             "launch_ms": launch_ms}
 
     sim.close()
+    if rank == 0 and not args.no_pattern and args.precision == "fp32" and args.workload == "roofline":
+        torch.cuda.empty_cache()
+        roof["pattern_ceiling"] = pattern_ceiling(args.size, achieved)
     forms = None
     if rank == 0 and not args.no_precision and args.precision == "fp32" and args.workload == "roofline":
         forms = precision_forms(args, prob, phi0_dev, stream, peak)

@@ -2,8 +2,10 @@
 
 Every translation unit is compiled in parallel with
 ``nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` and linked into
-one shared library exporting the C ABI of include/lbm.h.  Nothing here needs a
-GPU: nvcc cross-compiles.
+one shared library exporting the C ABI of include/lbm.h; alongside, the
+stand-alone ``pattern_probe`` program (the bandwidth ceiling of the step's
+streaming pattern, run by bench.py).  Nothing here needs a GPU: nvcc
+cross-compiles.
 """
 from __future__ import annotations
 
@@ -20,6 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIBRARY = os.path.join(LIBDIR, "liblbm.so")
+PROBE = os.path.join(LIBDIR, "pattern_probe")  # streaming-pattern bandwidth ceiling (pattern_probe.cu)
 
 SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_aux.cu", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_unfused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -48,7 +51,7 @@ def _inputs():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIBRARY) or not os.path.exists(STAMP):
+    if not os.path.exists(LIBRARY) or not os.path.exists(STAMP) or not os.path.exists(PROBE):
         return False
     if open(STAMP).read() != " ".join(extra_flags()):
         return False
@@ -66,13 +69,24 @@ def _compile(src: str, ptxas_verbose: bool) -> tuple:
     return obj, r.stderr
 
 
+def _compile_probe() -> tuple:
+    cmd = [nvcc()] + ARCH + ["-O3", "-std=c++17", os.path.join(CSRC, "pattern_probe.cu"), "-o", PROBE + ".tmp"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for pattern_probe.cu:\n{r.stdout}\n{r.stderr}")
+    os.replace(PROBE + ".tmp", PROBE)
+    return PROBE, r.stderr
+
+
 def build(force: bool = False, ptxas_verbose: bool = False) -> str:
     """Compiles (if stale) and returns the path of liblbm.so."""
     if not force and not ptxas_verbose and up_to_date():
         return LIBRARY
     os.makedirs(OBJDIR, exist_ok=True)
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        probe = ex.submit(_compile_probe)
         results = list(ex.map(lambda s: _compile(s, ptxas_verbose), SOURCES))
+        probe.result()
     if ptxas_verbose:
         for _, log in results:
             print(log)

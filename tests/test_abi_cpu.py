@@ -271,3 +271,16 @@ def test_large_box_limits(lbm):
     with pytest.raises(lbm.LBMError) as ei:
         lbm.lbm_workspace_size(lbm.make_domain(576, 576, 544, q_hydro=27, q_phase=27), lbm.make_params())
     assert ei.value.status == lbm.LBM_ERR_ARG
+
+
+def test_pattern_probe_is_built_and_checks_its_arguments(lbm):
+    """build() also makes the stand-alone streaming-pattern probe; it refuses box
+    sizes it does not handle before touching CUDA (exit status 2)."""
+    import os
+
+    from paper_2012_06144_gb300 import _build
+
+    assert os.access(_build.PROBE, os.X_OK)
+    for bad in (["48"], ["1024"], ["16"], ["64", "0"]):
+        r = subprocess.run([_build.PROBE] + bad, capture_output=True, text=True, timeout=60)
+        assert r.returncode == 2, (bad, r.stderr)
