@@ -304,7 +304,7 @@ def batched_form(args, stream, peak):
     for m, (_, phi0, _) in zip(batch.members, draws):
         m.init_phase(phi0)
     cells = batch.cells
-    shape, order, tune_ms = batch.tune(trial_steps=5)
+    shape, order, halo, tune_ms = batch.tune(trial_steps=5)
     batch.step(32)
     batch.synchronize()
     steps = args.batched_steps
@@ -329,9 +329,10 @@ def batched_form(args, stream, peak):
     bpc = bytes_per_cell(27, "fp32")
     out = {"members": len(batch), "cells": cells, "steps": steps, "value": cells / (ms / 1e3) / 1e6, "unit": UNIT,
            "ms_per_step": ms, "roofline_frac": cells * bpc / (ms / 1e3) / 1e9 / peak,
-           "tuned": {"tile": f"32x{shape[0]}x{shape[1]}", "order": order,
-                     "candidates_ms_per_step": {f"32x{lbm.BATCH_SHAPES[i // 2][0]}x{lbm.BATCH_SHAPES[i // 2][1]}/"
-                                                f"{lbm.BATCH_ORDERS[i % 2]}": float(v) for i, v in enumerate(tune_ms)}},
+           "tuned": {"tile": f"32x{shape[0]}x{shape[1]}", "order": order, "halo": halo,
+                     "candidates_ms_per_step": {
+                         "{2}/32x{0[0]}x{0[1]}/{1}".format(*lbm.batch_candidate(i)): float(v)
+                         for i, v in enumerate(tune_ms)}},
            "per_member_launches": {"value": cells / (solo_ms / 1e3) / 1e6, "ms_per_step": solo_ms,
                                    "steps": solo_steps},
            "gpu_launches_per_step": (len(batch) + 63) // 64,

@@ -248,17 +248,30 @@ lbm_t *lbm_batch_member(lbm_batch_t *b, int i);
  * on first use (so the first call of a run may take longer). */
 lbm_status lbm_batch_step(lbm_batch_t *b, int64_t n);
 
-/* Autotuner: for each of 3 tile shapes (TY, TZ) = (4, 2), (8, 1), (2, 4) and
- * each of 2 table orders (0: member after member; 1: members' tiles dealt out
- * round robin) runs 1 + trial_steps batched steps, times the trial steps with
- * CUDA events, and keeps the fastest pair.  The trial steps are real time
- * steps: every member advances by 6 (1 + trial_steps).  choice (may be NULL)
- * receives shape * 2 + order of the winner; ms_per_step (may be NULL) receives
- * the 6 measured times in the same order.  Synchronises the stream. */
+/* Autotuner (the tile shapes and the halo staging of the batched step): for
+ * each of 2 phi halo stagings (0: per-thread loads; 1: one TMA tensor copy per
+ * block, walled faces mirrored in shared memory, per-thread loads for tiles on
+ * a periodic face), 3 tile shapes (TY, TZ) = (4, 2), (8, 1), (2, 4) and 2 table
+ * orders (0: member after member; 1: members' tiles dealt out round robin),
+ * runs 1 + trial_steps batched steps, times the trial steps with CUDA events,
+ * and keeps the fastest.  Candidate index: (halo * 3 + shape) * 2 + order.  The
+ * trial steps are real time steps: every member advances by 1 + trial_steps per
+ * timed candidate.  The TMA staging needs every member's nx to be a multiple of
+ * 4 (and the driver's tensor-map support); otherwise its 6 candidates are
+ * skipped and reported as -1.  choice (may be NULL) receives the winner's
+ * index; ms_per_step (may be NULL) receives the 12 times by index.
+ * Synchronises the stream. */
 lbm_status lbm_batch_tune(lbm_batch_t *b, int trial_steps, int *choice, double *ms_per_step);
 
+/* Selects candidate `choice` of lbm_batch_tune (same index) without timing.
+ * LBM_ERR_ARG if choice is outside 0..11; LBM_ERR_STATE if it asks for the TMA
+ * staging and these members do not allow it.  Host-only apart from uploading
+ * the tile table (synchronises the stream). */
+lbm_status lbm_batch_set_config(lbm_batch_t *b, int choice);
+
 /* lbm_synchronize on every member: LBM_ERR_DIVERGED if any member produced a
- * non-finite phi or p* (lbm_last_error on that member says which). */
+ * non-finite phi or p*, LBM_ERR_CUDA if a TMA copy of a member's phi tile did
+ * not complete (lbm_last_error on that member says which). */
 lbm_status lbm_batch_synchronize(lbm_batch_t *b);
 
 /* Text of the last failure of a batch call on b. */

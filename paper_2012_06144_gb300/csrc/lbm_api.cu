@@ -280,7 +280,7 @@ lbm_status lbm_create(lbm_t **out, const lbm_domain *dom, const lbm_params *prm,
     s->cur = 0;
     s->t = 0;
     s->ready = false;
-    cudaError_t e = cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream);
+    cudaError_t e = cudaMemsetAsync(s->flag, 0, 2 * sizeof(int), s->stream);
     if (e != cudaSuccess) {
         g_create_error = std::string("cudaMemsetAsync: ") + cudaGetErrorString(e);
         if (s->owns_ws) cudaFree(s->ws);
@@ -297,7 +297,7 @@ lbm_status lbm_init_phase(lbm_t *s, const float *phi0, int phi0_on_device) {
     LBM_CK(s, cudaMemcpyAsync(s->phi[0], phi0, plane_bytes(s), kind_to_device(phi0_on_device), s->stream));
     if (!phi0_on_device) LBM_CK(s, cudaStreamSynchronize(s->stream));
     LBM_CK(s, lbm::launch_init(s->kp, s->sto, s->dom.q_hydro, s->dom.q_phase, s->phi[0], s->stream));
-    LBM_CK(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
+    LBM_CK(s, cudaMemsetAsync(s->flag, 0, 2 * sizeof(int), s->stream));
     // time level 0: the first phase-field step alone (u_{-1} = 0, phi^{-1} = phi0)
     if (s->unfused) {
         LBM_CK(s, cudaMemsetAsync(s->uf.u, 0, 3 * plane_bytes(s), s->stream));
@@ -421,7 +421,7 @@ lbm_status lbm_set_state(lbm_t *s, const float *h, const float *g, const float *
         LBM_CK(s, cudaMemcpyAsync(s->phi[s->cur], phi, plane_bytes(s), cudaMemcpyHostToDevice, s->stream));
         LBM_CK(s, cudaStreamSynchronize(s->stream));
     }
-    LBM_CK(s, cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
+    LBM_CK(s, cudaMemsetAsync(s->flag, 0, 2 * sizeof(int), s->stream));
     s->ready = true;
     return LBM_OK;
 }
@@ -429,10 +429,11 @@ lbm_status lbm_set_state(lbm_t *s, const float *h, const float *g, const float *
 lbm_status lbm_synchronize(lbm_t *s) {
     if (!s) return LBM_ERR_ARG;
     DeviceGuard dg(s->device);
-    int flag = 0;
-    LBM_CK(s, cudaMemcpyAsync(&flag, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    int flag[2] = {0, 0};  // [0] divergence, [1] a TMA copy of the phi tile that did not complete (batch)
+    LBM_CK(s, cudaMemcpyAsync(flag, s->flag, sizeof(flag), cudaMemcpyDeviceToHost, s->stream));
     LBM_CK(s, cudaStreamSynchronize(s->stream));
-    if (flag) return s->err = "non-finite phi or p* produced on the device", LBM_ERR_DIVERGED;
+    if (flag[1]) return s->err = "a TMA copy of the phi halo tile did not complete on the device", LBM_ERR_CUDA;
+    if (flag[0]) return s->err = "non-finite phi or p* produced on the device", LBM_ERR_DIVERGED;
     return LBM_OK;
 }
 

@@ -26,26 +26,35 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "lbm_handle.h"
 #include "lbm_step_impl.cuh"
 
 namespace lbm {
 
-constexpr int kGroup = 64;  // members per launch: 64 descriptors fit the 32 KB parameter block
+constexpr int kGroup = 64;  // members per launch: 64 descriptors and tensor-map pairs fit the 32 KB parameter block
 constexpr int kGraphSteps = 16;
 
 // A member's lattices are addressed as the single-simulation kernel addresses
 // walled boxes: base pointers plus 32-bit plane offsets (every member passes
 // offsets32), which measured 2.2% faster on the batched workload than a table
 // of 42 plane pointers per member and keeps the descriptor small.
+//
+//
+// The phi halo tile is staged either by per-thread loads or by one TMA copy per
+// block (tensor maps of each member's two phi buffers for the current tile shape,
+// also in the parameter block); the autotuner times both.
 struct MemberDesc {
     Params p;
     float *h_rest, *h_mov, *g_rest, *g_mov;  // rest and first moving plane of each lattice
     float *phi[2];
-    int *flag;
+    int *flag;  // [0] divergence, [1] a TMA halo copy that did not complete
 };
 
 struct GroupArgs {
+    CUtensorMap phi_map[kGroup][2];  // phi[0], phi[1] as 3-D FP32 tensors, box kTmaRow x (TY + 2) x (TZ + 2)
     MemberDesc m[kGroup];
 };
 static_assert(sizeof(GroupArgs) + 32 <= 32764, "kernel parameter block limit");
@@ -56,47 +65,95 @@ struct TileShape {
 constexpr TileShape kShapes[] = {{4, 2}, {8, 1}, {2, 4}};
 constexpr int kNumShapes = 3;
 constexpr int kNumOrders = 2;  // 0: member after member, 1: members interleaved tile by tile
+constexpr int kNumHalos = 2;   // 0: per-thread loads, 1: TMA copy (per-thread loads on periodic faces)
 
 // One block per entry tiles[blockIdx.x] = (member within the group, bx, by, bz).
-template <int QG, bool G_SW, bool H_SW, int TY, int TZ>
+template <int QG, bool G_SW, bool H_SW, int TY, int TZ, int HALO>
 __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
     batch_step_kernel(const __grid_constant__ GroupArgs a, const int4 *__restrict__ tiles, int cur) {
-    __shared__ float tile[TZ + 2][TY + 2][TX + 2];
+    constexpr int HW = HALO ? kTmaRow : TX + 2;
+    __shared__ __align__(128) float tile[TZ + 2][TY + 2][HW];
+    __shared__ uint64_t bar;
     const int4 e = tiles[blockIdx.x];
     const MemberDesc &d = a.m[e.x];
     const BaseLat32<float> lh{d.h_rest, d.h_mov, (unsigned)d.p.N}, lg{d.g_rest, d.g_mov, (unsigned)d.p.N};
-    tile_update<float, QG, 15, G_SW, H_SW, true, false, TY, TZ, true>(d.p, lh, lg, d.phi[cur], d.phi[cur ^ 1], d.flag,
-                                                                     tile, e.y, e.z, e.w, threadIdx.x, threadIdx.y,
-                                                                     threadIdx.z);
+    const HaloTma t{&bar, d.flag + 1};
+    const HaloTma *tma = nullptr;
+    if (HALO && tma_halo_fits<TY, TZ>(d.p, e.y, e.z, e.w)) {  // block-uniform
+        const bool lead = threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
+        if (lead) tma_bar_init(&bar);
+        __syncthreads();
+        if (lead)
+            tma_load_tile(&tile[0][0][0], &a.phi_map[e.x][cur], e.y * TX - 4, e.z * TY - 1, e.w * TZ - 1, &bar,
+                          (unsigned)sizeof(tile));
+        tma = &t;
+    }
+    tile_update<float, QG, 15, G_SW, H_SW, true, false, TY, TZ, true, HW>(d.p, lh, lg, d.phi[cur], d.phi[cur ^ 1],
+                                                                         d.flag, tile, e.y, e.z, e.w, threadIdx.x,
+                                                                         threadIdx.y, threadIdx.z, tma);
 }
 
 template <int QG, bool G_SW, bool H_SW, int TY, int TZ>
-static cudaError_t launch_shape(const GroupArgs &a, const int4 *tiles, int ntiles, int cur, cudaStream_t st) {
-    batch_step_kernel<QG, G_SW, H_SW, TY, TZ><<<ntiles, dim3(TX, TY, TZ), 0, st>>>(a, tiles, cur);
+static cudaError_t launch_shape(int halo, const GroupArgs &a, const int4 *tiles, int ntiles, int cur,
+                                cudaStream_t st) {
+    if (halo)
+        batch_step_kernel<QG, G_SW, H_SW, TY, TZ, 1><<<ntiles, dim3(TX, TY, TZ), 0, st>>>(a, tiles, cur);
+    else
+        batch_step_kernel<QG, G_SW, H_SW, TY, TZ, 0><<<ntiles, dim3(TX, TY, TZ), 0, st>>>(a, tiles, cur);
     return cudaGetLastError();
 }
 
 template <int QG, bool G_SW, bool H_SW>
-static cudaError_t launch_q(int shape, const GroupArgs &a, const int4 *tiles, int ntiles, int cur, cudaStream_t st) {
+static cudaError_t launch_q(int shape, int halo, const GroupArgs &a, const int4 *tiles, int ntiles, int cur,
+                            cudaStream_t st) {
     switch (shape) {
-        case 0: return launch_shape<QG, G_SW, H_SW, 4, 2>(a, tiles, ntiles, cur, st);
-        case 1: return launch_shape<QG, G_SW, H_SW, 8, 1>(a, tiles, ntiles, cur, st);
-        case 2: return launch_shape<QG, G_SW, H_SW, 2, 4>(a, tiles, ntiles, cur, st);
+        case 0: return launch_shape<QG, G_SW, H_SW, 4, 2>(halo, a, tiles, ntiles, cur, st);
+        case 1: return launch_shape<QG, G_SW, H_SW, 8, 1>(halo, a, tiles, ntiles, cur, st);
+        case 2: return launch_shape<QG, G_SW, H_SW, 2, 4>(halo, a, tiles, ntiles, cur, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 // g is read swapped on odd time levels; h runs one AA step ahead (opposite layout).
-static cudaError_t launch_group(int q_hydro, bool g_sw, int shape, const GroupArgs &a, const int4 *tiles,
+static cudaError_t launch_group(int q_hydro, bool g_sw, int shape, int halo, const GroupArgs &a, const int4 *tiles,
                                 int ntiles, int cur, cudaStream_t st) {
     if (ntiles == 0) return cudaSuccess;
     if (q_hydro == 19)
-        return g_sw ? launch_q<19, true, false>(shape, a, tiles, ntiles, cur, st)
-                    : launch_q<19, false, true>(shape, a, tiles, ntiles, cur, st);
+        return g_sw ? launch_q<19, true, false>(shape, halo, a, tiles, ntiles, cur, st)
+                    : launch_q<19, false, true>(shape, halo, a, tiles, ntiles, cur, st);
     if (q_hydro == 27)
-        return g_sw ? launch_q<27, true, false>(shape, a, tiles, ntiles, cur, st)
-                    : launch_q<27, false, true>(shape, a, tiles, ntiles, cur, st);
+        return g_sw ? launch_q<27, true, false>(shape, halo, a, tiles, ntiles, cur, st)
+                    : launch_q<27, false, true>(shape, halo, a, tiles, ntiles, cur, st);
     return cudaErrorInvalidValue;
+}
+
+// cuTensorMapEncodeTiled from the driver (through the runtime, no link to libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// The tensor map of one phi buffer of an nx x ny x nz box for the TMA halo tile of
+// shape (ty, tz); false if the box does not allow it (rows must be a multiple of
+// 16 bytes) or the driver refuses.
+bool encode_phi_map(CUtensorMap *m, float *phi, const lbm_domain &d, int ty, int tz) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || d.nx % 4 != 0 || ((uintptr_t)phi & 15) != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.nx * 4, (cuuint64_t)d.nx * d.ny * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kTmaRow, (cuuint32_t)(ty + 2), (cuuint32_t)(tz + 2)};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, phi, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace lbm
@@ -111,6 +168,9 @@ struct lbm_batch_t {
     std::vector<int> g_off, g_len;       // each group's range in the table
     int max_tiles = 0;
     int shape = 0, order = 0, table_key = -1;
+    int halo = 0;         // phi halo staging: 0 per-thread loads, 1 TMA copy
+    bool tma_ok = false;  // every member's phi buffers have tensor maps
+    int map_shape = -1;   // the tile shape the tensor maps were encoded for
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // key: (t & 1) * 2 + cur
     std::string err;
 };
@@ -155,6 +215,16 @@ void drop_graphs(lbm_batch_t *b) {
 lbm_status build_table(lbm_batch_t *b, int shape, int order) {
     const int key = shape * lbm::kNumOrders + order;
     if (b->table_key == key) return LBM_OK;
+    if (b->tma_ok && b->map_shape != shape) {  // the TMA box is part of the tensor map
+        const lbm::TileShape sh = lbm::kShapes[shape];
+        for (size_t i = 0; i < b->m.size() && b->tma_ok; ++i) {
+            CUtensorMap *maps = b->groups[i / lbm::kGroup].phi_map[i % lbm::kGroup];
+            for (int c = 0; c < 2 && b->tma_ok; ++c)
+                b->tma_ok = lbm::encode_phi_map(&maps[c], b->m[i]->phi[c], b->m[i]->dom, sh.ty, sh.tz);
+        }
+        b->map_shape = b->tma_ok ? shape : -1;
+        if (!b->tma_ok) b->halo = 0;
+    }
     std::vector<int4> t;
     t.reserve(b->max_tiles);
     const int nm = (int)b->m.size();
@@ -204,7 +274,7 @@ lbm_status check_lockstep(lbm_batch_t *b) {
 // the launches of one time step at level t with phi^t in phi[cur]
 cudaError_t enqueue_step(lbm_batch_t *b, int64_t t, int cur) {
     for (size_t g = 0; g < b->groups.size(); ++g) {
-        const cudaError_t e = lbm::launch_group(b->q_hydro, (t & 1) != 0, b->shape, b->groups[g],
+        const cudaError_t e = lbm::launch_group(b->q_hydro, (t & 1) != 0, b->shape, b->halo, b->groups[g],
                                                 b->d_tiles + b->g_off[g], b->g_len[g], cur, b->stream);
         if (e != cudaSuccess) return e;
     }
@@ -338,6 +408,7 @@ lbm_status lbm_batch_create(lbm_batch_t **out, int count, const lbm_domain *doms
         d.phi[1] = s->phi[1];
         d.flag = s->flag;
     }
+    b->tma_ok = lbm::tensor_map_encoder() != nullptr;
     const cudaError_t e = cudaMalloc(&b->d_tiles, (size_t)b->max_tiles * sizeof(int4));
     if (e != cudaSuccess) {
         lbm::set_thread_error(std::string("batch tile table: ") + cudaGetErrorString(e));
@@ -396,45 +467,76 @@ lbm_status lbm_batch_tune(lbm_batch_t *b, int trial_steps, int *choice, double *
         return b->err = "cudaEventCreate failed", LBM_ERR_CUDA;
     }
     double best = 1e300;
-    int best_shape = b->shape, best_order = b->order;
-    for (int sh = 0; sh < lbm::kNumShapes && st == LBM_OK; ++sh) {
-        for (int od = 0; od < lbm::kNumOrders && st == LBM_OK; ++od) {
-            st = build_table(b, sh, od);
-            if (st != LBM_OK) break;
-            b->shape = sh;
-            b->order = od;
-            cudaError_t e = enqueue_step(b, b->m[0]->t, b->m[0]->cur);  // untimed warm-up step
-            advance_all(b, 1);
-            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-            for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) {
-                e = enqueue_step(b, b->m[0]->t, b->m[0]->cur);
+    int best_shape = b->shape, best_order = b->order, best_halo = b->halo;
+    for (int ha = 0; ha < lbm::kNumHalos && st == LBM_OK; ++ha) {
+        for (int sh = 0; sh < lbm::kNumShapes && st == LBM_OK; ++sh) {
+            for (int od = 0; od < lbm::kNumOrders && st == LBM_OK; ++od) {
+                const int slot = (ha * lbm::kNumShapes + sh) * lbm::kNumOrders + od;
+                st = build_table(b, sh, od);
+                if (st != LBM_OK) break;
+                if (ha == 1 && !b->tma_ok) {  // no tensor maps for these members
+                    if (ms_per_step) ms_per_step[slot] = -1.0;
+                    continue;
+                }
+                if (b->halo != ha) drop_graphs(b);
+                b->shape = sh;
+                b->order = od;
+                b->halo = ha;
+                cudaError_t e = enqueue_step(b, b->m[0]->t, b->m[0]->cur);  // untimed warm-up step
                 advance_all(b, 1);
-            }
-            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                st = batch_fail(b, e, "batch tuning");
-                break;
-            }
-            const double per = ms / trial_steps;
-            if (ms_per_step) ms_per_step[sh * lbm::kNumOrders + od] = per;
-            if (per < best) {
-                best = per;
-                best_shape = sh;
-                best_order = od;
+                if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+                for (int k = 0; k < trial_steps && e == cudaSuccess; ++k) {
+                    e = enqueue_step(b, b->m[0]->t, b->m[0]->cur);
+                    advance_all(b, 1);
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    st = batch_fail(b, e, "batch tuning");
+                    break;
+                }
+                const double per = ms / trial_steps;
+                if (ms_per_step) ms_per_step[slot] = per;
+                if (per < best) {
+                    best = per;
+                    best_shape = sh;
+                    best_order = od;
+                    best_halo = ha;
+                }
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LBM_OK) return st;
-    b->shape = best_shape;
-    b->order = best_order;
     st = build_table(b, best_shape, best_order);
     if (st != LBM_OK) return st;
-    if (choice) *choice = best_shape * lbm::kNumOrders + best_order;
+    if (b->halo != best_halo) drop_graphs(b);
+    b->shape = best_shape;
+    b->order = best_order;
+    b->halo = b->tma_ok ? best_halo : 0;
+    if (choice) *choice = (b->halo * lbm::kNumShapes + best_shape) * lbm::kNumOrders + best_order;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_config(lbm_batch_t *b, int choice) {
+    if (!b) return LBM_ERR_ARG;
+    if (choice < 0 || choice >= lbm::kNumHalos * lbm::kNumShapes * lbm::kNumOrders)
+        return b->err = "configuration index out of range", LBM_ERR_ARG;
+    const int order = choice % lbm::kNumOrders, shape = (choice / lbm::kNumOrders) % lbm::kNumShapes,
+              halo = choice / (lbm::kNumOrders * lbm::kNumShapes);
+    BatchDeviceGuard dg(b->device);
+    const lbm_status st = build_table(b, shape, order);  // (re)encodes the tensor maps for the shape
+    if (st != LBM_OK) return st;
+    if (halo == 1 && !b->tma_ok)
+        return b->err = "TMA halo staging unavailable (a member's nx is not a multiple of 4, or no driver support)",
+               LBM_ERR_STATE;
+    if (b->halo != halo) drop_graphs(b);
+    b->shape = shape;
+    b->order = order;
+    b->halo = halo;
     return LBM_OK;
 }
 

@@ -378,13 +378,111 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh,
     pop_store_rest<T, QP, H_SW, EDGE>(lh, n, hv[0] - dsum);
 }
 
+// ---------------------------------------------------------------------------
+// The phi halo tile staged by the tensor-memory accelerator: one
+// cp.async.bulk.tensor load of a (TX + 8) x (TY + 2) x (TZ + 2) box starting at
+// (x0 - 4, y0 - 1, z0 - 1) (x0 - 4 keeps the copy on a 16-byte boundary; the
+// tile row is 40 floats with cell x0 at offset 4), completed on an mbarrier.
+// Coordinates outside the box read as 0: entries beyond a walled face are then
+// mirrored in shared memory (phi(-1) = phi(0), the neutral wetting of the
+// oracle), and tiles on a periodic face of the box are filled by per-thread
+// loads instead (their halo wraps around).
+constexpr int kTmaRow = TX + 8;
+constexpr int kTmaWaitLimit = 1 << 20;  // try_wait polls before the copy counts as lost
+
+struct HaloTma {
+    uint64_t *bar;  // the block's mbarrier (phase 0 completes when the tile has landed)
+    int *err;       // set to 1 if the copy did not complete within kTmaWaitLimit polls
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void tma_bar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// the arrival of the issuing thread with the byte count of the copy, then the copy
+__device__ __forceinline__ void tma_load_tile(float *dst, const void *tensor_map, int x, int y, int z, uint64_t *bar,
+                                              unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"(tensor_map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// bounded wait for phase 0 of the block's mbarrier
+__device__ __forceinline__ bool tma_bar_wait(uint64_t *bar) {
+    for (int k = 0; k < kTmaWaitLimit; ++k) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_addr(bar))
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// True if the tile's one-cell halo stays inside the box on every periodic axis
+// (the copy cannot wrap); walled axes are mirrored after the copy.
+template <int TY, int TZ>
+__device__ __forceinline__ bool tma_halo_fits(const Params &p, int bx, int by, int bz) {
+    const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
+    const bool ix = bx > 0 && (bx + 1) * TX < p.nx, iy = by > 0 && (by + 1) * TY < p.ny,
+               iz = bz > 0 && (bz + 1) * TZ < p.nz;
+    return (wx || ix) && (wy || iy) && (wz || iz);
+}
+
+// Mirror of the halo entries beyond the walled faces the tile touches: each takes
+// the value at its coordinates clamped into the box, an interior entry that the
+// copy delivered and that no thread writes here.
+template <int TY, int TZ, int HW>
+__device__ __forceinline__ void mirror_walls(const Params &p, float (*tile)[TY + 2][HW], int bx, int by, int bz,
+                                             int tid) {
+    constexpr int OX = HW == TX + 2 ? 1 : 4, NT = TX * TY * TZ, WX = TX + 2;
+    const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
+    const int gx0 = bx * TX - OX, gy0 = by * TY - 1, gz0 = bz * TZ - 1;
+    auto fix = [&](int kx, int ky, int kz) {
+        const int gx = gx0 + kx, gy = gy0 + ky, gz = gz0 + kz;
+        const int cx = wx ? min(max(gx, 0), p.nx - 1) : gx, cy = wy ? min(max(gy, 0), p.ny - 1) : gy,
+                  cz = wz ? min(max(gz, 0), p.nz - 1) : gz;
+        if (cx != gx || cy != gy || cz != gz) tile[kz][ky][kx] = tile[cz - gz0][cy - gy0][cx - gx0];
+    };
+    // x faces: the columns just outside the tile, every (y, z) row of the halo
+    if (wx && (bx == 0 || (bx + 1) * TX >= p.nx))
+        for (int e = tid; e < 2 * (TY + 2) * (TZ + 2); e += NT) {
+            const int r = e >> 1, ky = r % (TY + 2), kz = r / (TY + 2);
+            fix((e & 1) ? OX + min(TX, p.nx - bx * TX) : OX - 1, ky, kz);
+        }
+    // y faces and z faces: the rows / planes just outside, over the 34 needed columns
+    if (wy && (by == 0 || (by + 1) * TY >= p.ny))
+        for (int e = tid; e < 2 * WX * (TZ + 2); e += NT) {
+            const int r = e / WX, kx = OX - 1 + (e - r * WX), kz = r >> 1;
+            fix(kx, (r & 1) ? 1 + min(TY, p.ny - by * TY) : 0, kz);
+        }
+    if (wz && (bz == 0 || (bz + 1) * TZ >= p.nz))
+        for (int e = tid; e < 2 * WX * (TY + 2); e += NT) {
+            const int r = e / WX, kx = OX - 1 + (e - r * WX), ky = r >> 1;
+            fix(kx, ky, (r & 1) ? 1 + min(TZ, p.nz - bz * TZ) : 0);
+        }
+}
+
 template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, int EDGE, int TY, int TZ,
-          typename LH, typename LG>
+          int HW, typename LH, typename LG>
 __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const LG &lg, const Nb3 &n, bool active,
-                                            const float *__restrict__ phi_in, float (*tile)[TY + 2][TX + 2],
+                                            const float *__restrict__ phi_in, float (*tile)[TY + 2][HW],
                                             float *__restrict__ phi_out, int *__restrict__ flag, int bx, int by,
-                                            int bz, int tx, int ty, int tz) {
+                                            int bz, int tx, int ty, int tz, const HaloTma *tma) {
     constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
+    constexpr int OX = HW == TX + 2 ? 1 : 4;  // tile column of cell x0: 1 (34-float rows) or 4 (TMA rows)
+    static_assert(HW == TX + 2 || HW == kTmaRow, "tile row width");
     // the D2Q9 pair (nx x ny x 1 box): only the cell's own plane, kept as tile[1]
     constexpr bool PLANE = QP == 9;
 
@@ -401,7 +499,7 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
 #pragma unroll
     for (int k = 0; k < RPW; ++k) {
         const int r = warp + k * NWARP;
-        if (r < NROW) {
+        if (!tma && r < NROW) {
             const int kz = PLANE ? 1 : r / HY, ky = PLANE ? r : r - kz * HY;
             // coordinates beyond a ragged box end are clamped into the box; those
             // halo entries only feed threads that are inactive
@@ -429,16 +527,35 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
                                   : pop_load<T, QP, H_SW, EDGE>(lh, n, i, ch);
     }
 
+    if (!tma) {
 #pragma unroll
-    for (int k = 0; k < RPW; ++k) {
-        const int r = warp + k * NWARP;
-        if (r < NROW) {
-            const int kz = PLANE ? 1 : r / HY, ky = PLANE ? r : r - kz * HY;
-            tile[kz][ky][lane] = tv0[k];
-            if (lane < HX - 32) tile[kz][ky][32 + lane] = tv1[k];
+        for (int k = 0; k < RPW; ++k) {
+            const int r = warp + k * NWARP;
+            if (r < NROW) {
+                const int kz = PLANE ? 1 : r / HY, ky = PLANE ? r : r - kz * HY;
+                tile[kz][ky][OX - 1 + lane] = tv0[k];
+                if (lane < HX - 32) tile[kz][ky][OX + 31 + lane] = tv1[k];
+            }
+        }
+        __syncthreads();
+    } else {
+        // the copy issued at block start; then the mirror of walled faces, if any
+        const bool landed = tma_bar_wait(tma->bar);
+        const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
+        const bool walls = (wx && (bx == 0 || (bx + 1) * TX >= p.nx)) || (wy && (by == 0 || (by + 1) * TY >= p.ny)) ||
+                           (wz && (bz == 0 || (bz + 1) * TZ >= p.nz));
+        if (walls) {
+            if (__syncthreads_or(!landed)) {
+                if (tx == 0 && ty == 0 && tz == 0) *tma->err = 1;
+                return;
+            }
+            mirror_walls<TY, TZ, HW>(p, tile, bx, by, bz, tx + TX * (ty + TY * tz));
+            __syncthreads();
+        } else if (!landed) {
+            *tma->err = 1;
+            return;
         }
     }
-    __syncthreads();
     if (!active) return;
     float nb[27];
 #pragma unroll
@@ -447,7 +564,7 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
         for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx)
-                nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[PLANE ? 1 : tz + 1 + dz][ty + 1 + dy][tx + 1 + dx];
+                nb[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = tile[PLANE ? 1 : tz + 1 + dz][ty + 1 + dy][tx + OX + dx];
     collide_and_store<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, EDGE>(p, lh, lg, n, gv, hv, nb, phi_out, flag);
 }
 
@@ -457,12 +574,14 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
 // XONLY: a tile that touches only the x walls takes a path that tests the x walls
 // alone (the batched walled boxes, at most 64 cells wide, are mostly such tiles;
 // for the single-simulation kernel the extra path cost more than it saved).
+// HW / tma: the phi tile's row width (TX + 2, filled by per-thread loads; or
+// kTmaRow, with tma given when the block has issued the tile's TMA copy).
 template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool HYDRO, bool PMRT, int TY, int TZ, bool XONLY = false,
-          typename LH, typename LG>
+          int HW = TX + 2, typename LH, typename LG>
 __device__ __forceinline__ void tile_update(const Params &p, const LH &lh, const LG &lg,
                                             const float *__restrict__ phi_in, float *__restrict__ phi_out,
-                                            int *__restrict__ flag, float (*tile)[TY + 2][TX + 2], int bx, int by,
-                                            int bz, int tx, int ty, int tz) {
+                                            int *__restrict__ flag, float (*tile)[TY + 2][HW], int bx, int by,
+                                            int bz, int tx, int ty, int tz, const HaloTma *tma = nullptr) {
     const int x = bx * TX + tx;
     const int y = by * TY + ty;
     const int z = bz * TZ + tz;
@@ -490,14 +609,14 @@ __device__ __forceinline__ void tile_update(const Params &p, const LH &lh, const
     const bool ex = wx && (bx == 0 || (bx + 1) * TX >= p.nx), ey = wy && (by == 0 || (by + 1) * TY >= p.ny),
                ez = wz && (bz == 0 || (bz + 1) * TZ >= p.nz);
     if (!(ex || ey || ez))
-        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, 0, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag,
-                                                                   bx, by, bz, tx, ty, tz);
+        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, 0, TY, TZ, HW>(p, lh, lg, n, active, phi_in, tile, phi_out,
+                                                                       flag, bx, by, bz, tx, ty, tz, tma);
     else if (XONLY && !(ey || ez))
-        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, 1, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag,
-                                                                   bx, by, bz, tx, ty, tz);
+        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, 1, TY, TZ, HW>(p, lh, lg, n, active, phi_in, tile, phi_out,
+                                                                       flag, bx, by, bz, tx, ty, tz, tma);
     else
-        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, 7, TY, TZ>(p, lh, lg, n, active, phi_in, tile, phi_out, flag,
-                                                                   bx, by, bz, tx, ty, tz);
+        cell_update<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, 7, TY, TZ, HW>(p, lh, lg, n, active, phi_in, tile, phi_out,
+                                                                       flag, bx, by, bz, tx, ty, tz, tma);
 }
 
 }  // namespace lbm

@@ -78,12 +78,26 @@ _SIGNATURES = {
     "lbm_batch_member": ([_VP, ctypes.c_int], _VP),
     "lbm_batch_step": ([_VP, ctypes.c_int64], ctypes.c_int),
     "lbm_batch_tune": ([_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP], ctypes.c_int),
+    "lbm_batch_set_config": ([_VP, ctypes.c_int], ctypes.c_int),
     "lbm_batch_synchronize": ([_VP], ctypes.c_int),
     "lbm_batch_last_error": ([_VP], ctypes.c_char_p),
     "lbm_batch_destroy": ([_VP], None),
 }
 BATCH_SHAPES = [(4, 2), (8, 1), (2, 4)]  # (TY, TZ) of the autotuner's tile shapes, in its order
 BATCH_ORDERS = ["member", "round_robin"]
+BATCH_HALOS = ["loads", "tma"]  # phi halo staging: per-thread loads, or one TMA tensor copy per block
+
+
+def batch_choice(shape, order, halo="loads") -> int:
+    """Candidate index of lbm_batch_tune / lbm_batch_set_config."""
+    return (BATCH_HALOS.index(halo) * len(BATCH_SHAPES) + BATCH_SHAPES.index(tuple(shape))) * len(BATCH_ORDERS) + \
+        BATCH_ORDERS.index(order)
+
+
+def batch_candidate(choice: int):
+    """(shape (TY, TZ), order name, halo name) of a candidate index."""
+    no, ns = len(BATCH_ORDERS), len(BATCH_SHAPES)
+    return BATCH_SHAPES[(choice // no) % ns], BATCH_ORDERS[choice % no], BATCH_HALOS[choice // (no * ns)]
 
 
 def header_functions() -> list:
@@ -270,9 +284,13 @@ def lbm_batch_step(b, n: int):
 def lbm_batch_tune(b, trial_steps: int = 5):
     """(choice, ms_per_step[6]) -- choice = shape * 2 + order."""
     choice = ctypes.c_int(-1)
-    ms = np.zeros(len(BATCH_SHAPES) * len(BATCH_ORDERS))
+    ms = np.zeros(len(BATCH_HALOS) * len(BATCH_SHAPES) * len(BATCH_ORDERS))
     _check_batch(load().lbm_batch_tune(b, int(trial_steps), ctypes.byref(choice), ms.ctypes.data_as(_DP)), b)
     return choice.value, ms
+
+
+def lbm_batch_set_config(b, choice: int):
+    _check_batch(load().lbm_batch_set_config(b, int(choice)), b)
 
 
 def lbm_batch_synchronize(b):
@@ -437,12 +455,17 @@ class Batch:
         lbm_batch_step(self.handle, n)
 
     def tune(self, trial_steps: int = 5):
-        """Times every (tile shape, table order) on the batch -- the trial steps
-        advance every member -- and keeps the fastest.  Returns
-        (shape (TY, TZ), order name, ms_per_step for all candidates)."""
+        """Times every (halo staging, tile shape, table order) on the batch -- the
+        trial steps advance every member -- and keeps the fastest.  Returns
+        (shape (TY, TZ), order name, halo name, ms_per_step for all candidates,
+        -1 where the TMA staging is unavailable)."""
         choice, ms = lbm_batch_tune(self.handle, trial_steps)
-        no = len(BATCH_ORDERS)
-        return BATCH_SHAPES[choice // no], BATCH_ORDERS[choice % no], ms
+        shape, order, halo = batch_candidate(choice)
+        return shape, order, halo, ms
+
+    def configure(self, shape=(4, 2), order="member", halo="loads"):
+        """Selects one candidate of the tuner without timing."""
+        lbm_batch_set_config(self.handle, batch_choice(shape, order, halo))
 
     def synchronize(self):
         lbm_batch_synchronize(self.handle)

@@ -132,19 +132,104 @@ def test_members_match_single_runs(lbm, orc, stream, q):
 
 def test_tuner_visits_every_candidate(lbm, orc, stream):
     """The tuner's trial steps are real steps through all 3 tile shapes x 2 table
-    orders; the members must still match single runs afterwards."""
+    orders; these members (nx not a multiple of 4) have no TMA staging, so its 6
+    candidates are skipped.  The members must still match single runs afterwards."""
     members = _members(27)
     batch = lbm.Batch.from_problems([p for p, _ in members], stream=stream)
     for m, (_, phi0) in zip(batch.members, members):
         m.init_phase(phi0)
-    shape, order, ms = batch.tune(trial_steps=2)
-    assert shape in lbm.BATCH_SHAPES and order in lbm.BATCH_ORDERS
-    assert ms.shape == (6,) and np.all(ms > 0)
+    shape, order, halo, ms = batch.tune(trial_steps=2)
+    assert shape in lbm.BATCH_SHAPES and order in lbm.BATCH_ORDERS and halo == "loads"
+    assert ms.shape == (12,) and np.all(ms[:6] > 0) and np.all(ms[6:] == -1.0)
     assert batch.steps_done() == 6 * 3
+    with pytest.raises(lbm.LBMError) as e:
+        batch.configure((4, 2), "member", "tma")
+    assert e.value.status == lbm.LBM_ERR_STATE
     batch.step(17)  # the chosen candidate, graph and plain
     batch.synchronize()
     for m, (prob, phi0) in zip(batch.members, members):
         _assert_as_close_as_single(orc, lbm, m, prob, phi0, 6 * 3 + 17)
+    batch.close()
+
+
+def _tma_members(q):
+    """Members whose rows suit the TMA staging (nx a multiple of 4): several x
+    tiles and a ragged x tail, ragged y / z tails, walled and periodic faces on
+    every axis (periodic-face tiles fall back to per-thread loads)."""
+    specs = [
+        ((36, 29, 19), (1, 1, 1), dict(rho_ratio=100.0, mu_ratio=30.0, sigma=1e-3, xi=3.0, mobility=0.03,
+                                       gravity=(1e-5, -2e-5, 3e-6), rho_ref=0.4), False),
+        ((96, 17, 11), (0, 0, 0), dict(rho_ratio=1000.0, sigma=5e-4, xi=4.0, gravity=(0.0, -1e-5, 0.0),
+                                       rho_ref=1.0, clamp_phi=1), False),
+        ((64, 13, 10), (1, 0, 1), dict(rho_ratio=10.0, mu_ratio=5.0, nu_H=0.05, sigma=1e-4), True),
+        ((8, 9, 7), (0, 1, 0), dict(rho_ratio=10.0, sigma=1e-4, xi=3.0), True),
+        ((100, 12, 9), (1, 1, 0), dict(rho_ratio=1000.0, nu_H=0.02, mobility=0.05, gravity=(0.0, 0.0, 2e-6),
+                                       rho_ref=1.0, clamp_phi=1), False),
+    ]
+    out = []
+    for (nx, ny, nz), wall, kw, heavy in specs:
+        prob = W.Problem(nx, ny, nz, wall=wall, q_hydro=q, **kw)
+        r = max(1.0, min(nx, ny, nz) / 3.0)
+        phi0 = W.sphere_phi(prob, (nx / 2, ny / 2, nz / 2), r, heavy_inside=heavy).astype(np.float32)
+        out.append((prob, phi0))
+    return out
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("shape", [(4, 2), (8, 1), (2, 4)])
+def test_tma_halo_staging(lbm, orc, stream, q, shape):
+    """The TMA-staged phi tile feeds the same stencil values as per-thread loads:
+    one step from a random state agrees with the loads' step to FP32 rounding (the
+    two kernels may contract multiply-adds differently) and with the FP64 oracle;
+    after plain and graph-replayed steps every member is as close to the oracle
+    as a single run."""
+    members = _tma_members(q)
+    states = [W.random_state(p, seed=31 + k) for k, (p, _) in enumerate(members)]
+    got = {}
+    for halo in ("loads", "tma"):
+        batch = lbm.Batch.from_problems([p for p, _ in members], stream=stream)
+        batch.configure(shape, "member", halo)
+        for m, st in zip(batch.members, states):
+            m.set_state(*st)
+        batch.step(1)
+        batch.synchronize()
+        got[halo] = [m.get_state() for m in batch.members]
+        batch.close()
+    for (prob, _), st, a, b in zip(members, states, got["loads"], got["tma"]):
+        h, g, phi = st
+        op = orc.make_problem(prob)
+        g1, u = orc.hydro_step(op, g.astype(np.float64), phi.astype(np.float64))
+        h1, phi1 = orc.phase_step(op, h.astype(np.float64), phi.astype(np.float64), u)
+        for x, y, ref in zip(a, b, (h1, g1, phi1)):
+            scale = np.abs(ref).max()
+            assert np.abs(x - y).max() <= 1e-6 * scale
+            assert np.abs(y - ref).max() <= TOL * scale
+    batch = lbm.Batch.from_problems([p for p, _ in members], stream=stream)
+    batch.configure(shape, "round_robin", "tma")
+    for m, (_, phi0) in zip(batch.members, members):
+        m.init_phase(phi0)
+    batch.step(3)
+    batch.step(16)
+    batch.synchronize()
+    for m, (prob, phi0) in zip(batch.members, members):
+        _assert_as_close_as_single(orc, lbm, m, prob, phi0, 19)
+    batch.close()
+
+
+def test_tuner_with_tma_candidates(lbm, orc, stream):
+    """With TMA-capable members the tuner times all 12 candidates."""
+    members = _tma_members(27)
+    batch = lbm.Batch.from_problems([p for p, _ in members], stream=stream)
+    for m, (_, phi0) in zip(batch.members, members):
+        m.init_phase(phi0)
+    shape, order, halo, ms = batch.tune(trial_steps=2)
+    assert ms.shape == (12,) and np.all(ms > 0)
+    assert halo in lbm.BATCH_HALOS
+    assert batch.steps_done() == 12 * 3
+    batch.step(5)
+    batch.synchronize()
+    for m, (prob, phi0) in zip(batch.members, members):
+        _assert_as_close_as_single(orc, lbm, m, prob, phi0, 12 * 3 + 5)
     batch.close()
 
 
