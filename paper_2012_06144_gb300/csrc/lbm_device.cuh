@@ -70,6 +70,15 @@ __host__ __device__ constexpr V3 vel(int i) {
 
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
+// D3Q27 index of the direction (x, y, z) in {-1, 0, 1}^3
+__host__ __device__ constexpr int idx27(int x, int y, int z) {
+    for (int i = 0; i < 27; ++i) {
+        const V3 e = vel27(i);
+        if (e.x == x && e.y == y && e.z == z) return i;
+    }
+    return -1;
+}
+
 // Lattice weights selected by |e|^2.
 template <int Q>
 __host__ __device__ constexpr float wgt(int i) {
@@ -319,24 +328,64 @@ struct Hydro {
 // SCALED: gv holds the populations multiplied by p.g_scale (a power of two, the
 // 16-bit storage units); the moment sums are taken in those units and brought
 // back with one multiplication each, which is exact.
-template <int QG, bool SCALED = false>
+// CASCADE (D3Q27): the moments by sums along x, then y, then z -- 66 additions
+// instead of 111 over opposite pairs.  Same GPU, same process, 512^3: +2.7 % for
+// the issue-bound FP16 step, but -5.3 % for FP32 and -1.0 % for BF16 (register
+// allocation), so only the FP16 step takes it.
+template <int QG, bool SCALED = false, bool CASCADE = false>
 __device__ __forceinline__ void hydro_macro(const Params &p, const float gv[QG], float phi, const Stencil &S,
                                             Hydro<QG> &H) {
     // moments of g over opposite pairs: s = g_i + g_opp(i) carries the even
     // moments (p*, second moments), d = g_i - g_opp(i) the odd ones (j)
     float ps = gv[0], jx = 0.f, jy = 0.f, jz = 0.f, mxx = 0.f, myy = 0.f, mzz = 0.f, mxy = 0.f, mxz = 0.f,
           myz = 0.f;
+    if constexpr (QG == 27 && CASCADE) {
+        // D3Q27 spans {-1, 0, 1}^3: the moments up to second order by sums along x,
+        // then y, then z
+        float X0[3][3], X1[3][3], X2[3][3];  // per (z, y) line: sum, first and second moment in x
 #pragma unroll
-    for (int i = 1; i < QG; i += 2) {
-        const V3 e = vel<QG>(i);
-        const float s = gv[i] + gv[i + 1], d = gv[i] - gv[i + 1];
-        ps += s;
-        if (e.x) { jx += e.x > 0 ? d : -d; mxx += s; }
-        if (e.y) { jy += e.y > 0 ? d : -d; myy += s; }
-        if (e.z) { jz += e.z > 0 ? d : -d; mzz += s; }
-        if (e.x && e.y) mxy += (e.x * e.y > 0) ? s : -s;
-        if (e.x && e.z) mxz += (e.x * e.z > 0) ? s : -s;
-        if (e.y && e.z) myz += (e.y * e.z > 0) ? s : -s;
+        for (int z = 0; z < 3; ++z)
+#pragma unroll
+            for (int y = 0; y < 3; ++y) {
+                const float a = gv[idx27(-1, y - 1, z - 1)], b = gv[idx27(0, y - 1, z - 1)],
+                            c = gv[idx27(1, y - 1, z - 1)];
+                X2[z][y] = a + c;
+                X0[z][y] = X2[z][y] + b;
+                X1[z][y] = c - a;
+            }
+        float Y00[3], Y01[3], Y02[3], Y10[3], Y11[3], Y20[3];  // Yab: x-moment a, y-moment b, per z
+#pragma unroll
+        for (int z = 0; z < 3; ++z) {
+            Y02[z] = X0[z][0] + X0[z][2];
+            Y00[z] = Y02[z] + X0[z][1];
+            Y01[z] = X0[z][2] - X0[z][0];
+            Y10[z] = (X1[z][0] + X1[z][2]) + X1[z][1];
+            Y11[z] = X1[z][2] - X1[z][0];
+            Y20[z] = (X2[z][0] + X2[z][2]) + X2[z][1];
+        }
+        mzz = Y00[0] + Y00[2];
+        ps = mzz + Y00[1];
+        jz = Y00[2] - Y00[0];
+        jy = (Y01[0] + Y01[2]) + Y01[1];
+        myz = Y01[2] - Y01[0];
+        myy = (Y02[0] + Y02[2]) + Y02[1];
+        jx = (Y10[0] + Y10[2]) + Y10[1];
+        mxz = Y10[2] - Y10[0];
+        mxy = (Y11[0] + Y11[2]) + Y11[1];
+        mxx = (Y20[0] + Y20[2]) + Y20[1];
+    } else {
+#pragma unroll
+        for (int i = 1; i < QG; i += 2) {
+            const V3 e = vel<QG>(i);
+            const float s = gv[i] + gv[i + 1], d = gv[i] - gv[i + 1];
+            ps += s;
+            if (e.x) { jx += e.x > 0 ? d : -d; mxx += s; }
+            if (e.y) { jy += e.y > 0 ? d : -d; myy += s; }
+            if (e.z) { jz += e.z > 0 ? d : -d; mzz += s; }
+            if (e.x && e.y) mxy += (e.x * e.y > 0) ? s : -s;
+            if (e.x && e.z) mxz += (e.x * e.z > 0) ? s : -s;
+            if (e.y && e.z) myz += (e.y * e.z > 0) ? s : -s;
+        }
     }
     if constexpr (SCALED) {
         const float r = p.g_inv_scale;

@@ -198,7 +198,8 @@ __device__ __forceinline__ float pop_load(const L &lat, const Nb3 &n, int i, con
 // FP16 storage: both lattices stay in their storage units through the step
 // (g times g_scale, h_i minus w_i phi_ref), which removes a decode and an encode
 // per population: +5.0 % at 512^3 in a same-GPU comparison.  BF16 keeps the
-// decode-compute-encode form, which measured 9 % faster for it there.
+// decode-compute-encode form, which measured 9 % faster for it there.  The FP16
+// step also takes the D3Q27 moments by the x-y-z cascade of hydro_macro.
 template <typename T>
 constexpr bool in_units() {
     return std::is_same<T, __half>::value;
@@ -249,7 +250,7 @@ __device__ __forceinline__ void collide_and_store(const Params &p, const LH &lh,
         // scaled once, so E +- O below is already the value to store.
         constexpr bool UNITS = in_units<T>();
         Hydro<QG> Hd;
-        hydro_macro<QG, UNITS>(p, gv, phic, S, Hd);
+        hydro_macro<QG, UNITS, UNITS>(p, gv, phic, S, Hd);
         HydroPost<QG> P = hydro_post<QG>(Hd);
         if constexpr (UNITS) scale_post<QG>(P, p.g_scale);
         // The rest population takes p* - sum_{i>0} g*_i, with each g*_i as the next
