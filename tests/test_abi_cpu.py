@@ -284,3 +284,18 @@ def test_pattern_probe_is_built_and_checks_its_arguments(lbm):
     for bad in (["48"], ["1024"], ["16"], ["64", "0"]):
         r = subprocess.run([_build.PROBE] + bad, capture_output=True, text=True, timeout=60)
         assert r.returncode == 2, (bad, r.stderr)
+
+
+def test_batch_candidate_index_round_trip(lbm):
+    """The binding's candidate index matches the C tuner's layout
+    (halo * 3 + shape) * 2 + order, over all 12 candidates, and the C entry point
+    refuses indices outside 0..11 without touching CUDA."""
+    seen = set()
+    for i in range(len(lbm.BATCH_HALOS) * len(lbm.BATCH_SHAPES) * len(lbm.BATCH_ORDERS)):
+        shape, order, halo = lbm.batch_candidate(i)
+        assert lbm.batch_choice(shape, order, halo) == i
+        assert i == (lbm.BATCH_HALOS.index(halo) * 3 + lbm.BATCH_SHAPES.index(shape)) * 2 + lbm.BATCH_ORDERS.index(order)
+        seen.add((shape, order, halo))
+    assert len(seen) == 12
+    lib = lbm.load()
+    assert lib.lbm_batch_set_config(None, 0) == lbm.LBM_ERR_ARG
