@@ -5,11 +5,12 @@
  * Method: Holzer, Bauer, Koestler, Ruede, "Highly efficient lattice Boltzmann
  * multiphase simulations of immiscible fluids at high-density ratios on CPUs and
  * GPUs through code generation", arXiv 2012.06144.
- *   - phase-field LB on D3Q15, or D3Q19 / D3Q27 for the other stencil pairs of
- *     Section 5.1 (Section 3.1, eq:lb_interface, eq:interfaceTracking,
+ *   - phase-field LB on D3Q15, or D3Q19 / D3Q27 (and the D2Q9 pair in two
+ *     dimensions) for the other stencil pairs of Section 5.1 (Section 3.1,
+ *     eq:lb_interface, eq:interfaceTracking,
  *     eq:updatePhaseField), single-relaxation-time collision with rate
  *     omega_phi = 1/(3 M + 1/2);
- *   - velocity-based hydrodynamic LB on D3Q19 or D3Q27 (Section 3.2, eq:lb_flow,
+ *   - velocity-based hydrodynamic LB on D3Q19 or D3Q27 (D2Q9 in the pair) (Section 3.2, eq:lb_flow,
  *     eq:forceHydro ... eq:updateVelocityField), weighted-orthogonal MRT with the
  *     force applied in moment space (eq:improved_collision);
  *   - isotropic stencils eq:grad and eq:lap;
@@ -23,7 +24,9 @@
  *     D3Q19/D3Q27 then 7..18 = edges (+x+y,-x-y,+x-y,-x+y, +x+z,-x-z,+x-z,-x+z,
  *     +y+z,-y-z,+y-z,-y+z); D3Q27 then 19..26 = corners (+++,---,++-,--+,+-+,-+-,
  *     -++,+--).  D3Q15 = rest, the six faces, then the eight corners as 7..14 in
- *     the same corner order.  Each moving direction is followed by its opposite.
+ *     the same corner order.  D2Q9 = rest, +x,-x,+y,-y, then the xy edges
+ *     +x+y,-x-y,+x-y,-x+y as 5..8.  Each moving direction is followed by its
+ *     opposite.
  *   - Walls: wall[a] = 1 puts no-slip walls (half-way bounce-back for h and g,
  *     mirrored ghost values of phi in the stencils) on both faces of axis a;
  *     wall[a] = 0 makes axis a periodic.
@@ -92,9 +95,11 @@ typedef struct {
                        165 M cells at D3Q27) need FP32 storage, the SRT phase
                        collision and the D3Q15 phase lattice                   */
     int wall[3];    /* 0 = periodic axis, 1 = no-slip walls on both faces       */
-    int q_phase;    /* 15 (the benchmarked pair), 19 or 27; 19 and 27 need FP32
+    int q_phase;    /* 15 (the benchmarked pair), 19 or 27; or 9 with q_hydro 9
+                       (the two-dimensional D2Q9 pair of Section 5.1: nz = 1,
+                       wall[2] = 0, gravity[2] = 0).  9, 19 and 27 need FP32
                        storage, the SRT phase collision and the fused form      */
-    int q_hydro;    /* 19 or 27                                                 */
+    int q_hydro;    /* 19 or 27; 9 only with q_phase 9                          */
 } lbm_domain;
 
 /* Physical parameters in lattice units (Delta x = Delta t = 1, c_s^2 = 1/3). */
@@ -148,7 +153,8 @@ enum {
 lbm_status lbm_workspace_size(const lbm_domain *dom, const lbm_params *prm, size_t *bytes);
 
 /* Validates the problem (Section 3 parameters; LBM_ERR_ARG on a non-positive
- * size, q_phase not 15/19/27, q_hydro not 19/27, non-positive densities, viscosities,
+ * size, q_phase not 9/15/19/27, q_hydro not 9/19/27, a D2Q9 lattice not paired with
+ * D2Q9 or on a box that is not nx x ny x 1 periodic in z, non-positive densities, viscosities,
  * xi or mobility, negative sigma, non-finite values), derives tau_H, tau_L,
  * omega_phi, beta, kappa and creates a handle on the current CUDA device.
  * cuda_stream: a cudaStream_t to enqueue all work on, or NULL for the legacy
