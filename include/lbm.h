@@ -263,7 +263,7 @@ lbm_status lbm_batch_step(lbm_batch_t *b, int64_t n);
  * and keeps the fastest.  Candidate index: (halo * 3 + shape) * 2 + order.  The
  * trial steps are real time steps: every member advances by 1 + trial_steps per
  * timed candidate.  The TMA staging needs every member's nx to be a multiple of
- * 4 (and the driver's tensor-map support); otherwise its 6 candidates are
+ * 4 (and the CUDA driver's tensor-map support); otherwise its 6 candidates are
  * skipped and reported as -1.  choice (may be NULL) receives the winner's
  * index; ms_per_step (may be NULL) receives the 12 times by index.
  * Synchronises the stream. */

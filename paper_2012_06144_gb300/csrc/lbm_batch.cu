@@ -127,7 +127,7 @@ static cudaError_t launch_group(int q_hydro, bool g_sw, int shape, int halo, con
     return cudaErrorInvalidValue;
 }
 
-// cuTensorMapEncodeTiled from the driver (through the runtime, no link to libcuda)
+// cuTensorMapEncodeTiled from the CUDA driver (through the runtime, no link to libcuda)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         void *f = nullptr;
@@ -143,7 +143,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // The tensor map of one phi buffer of an nx x ny x nz box for the TMA halo tile of
 // shape (ty, tz); false if the box does not allow it (rows must be a multiple of
-// 16 bytes) or the driver refuses.
+// 16 bytes) or the CUDA driver refuses.
 bool encode_phi_map(CUtensorMap *m, float *phi, const lbm_domain &d, int ty, int tz) {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || d.nx % 4 != 0 || ((uintptr_t)phi & 15) != 0) return false;
