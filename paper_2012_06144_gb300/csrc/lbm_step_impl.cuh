@@ -542,7 +542,6 @@ __device__ __forceinline__ void cell_update(const Params &p, const LH &lh, const
     } else {
         // the copy issued at block start; then the mirror of walled faces, if any
         const bool landed = tma_bar_wait(tma->bar);
-        const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
         const bool walls = (wx && (bx == 0 || (bx + 1) * TX >= p.nx)) || (wy && (by == 0 || (by + 1) * TY >= p.ny)) ||
                            (wz && (bz == 0 || (bz + 1) * TZ >= p.nz));
         if (walls) {
