@@ -226,15 +226,6 @@ __device__ __forceinline__ void pop_src_loc(const Cell &C, int i, int &slot, int
     idx = nbr(C, -e.x, -e.y, -e.z);
 }
 
-// Location that receives the post-collision f*_i(x).
-template <int Q, bool SWAPPED>
-__device__ __forceinline__ size_t pop_dst(const Cell &C, long long N, int i) {
-    if (!SWAPPED) return (size_t)opp(i) * N + C.c;
-    const V3 e = vel<Q>(i);
-    if (leaves(C, e, +1)) return (size_t)opp(i) * N + C.c;
-    return (size_t)i * N + nbr(C, e.x, e.y, e.z);
-}
-
 // The 3x3x3 neighbourhood of phi, nb[(dz+1)*9 + (dy+1)*3 + (dx+1)].
 __device__ __forceinline__ void gather_phi(const float *__restrict__ phi, const Cell &C, float nb[27]) {
 #pragma unroll

@@ -72,24 +72,6 @@ struct BaseLat32 {
     }
 };
 
-// Plane addresses of one lattice from its rest plane and first moving plane
-// (moving planes N elements apart).
-template <typename T>
-struct BaseLat {
-    float *rest;
-    T *mov;
-    long long N;
-    template <typename U>
-    __device__ __forceinline__ U *ptr(int s) const {
-        if (s == 0) return reinterpret_cast<U *>(rest);
-        return reinterpret_cast<U *>(mov + (size_t)(s - 1) * N);
-    }
-    template <typename U>
-    __device__ __forceinline__ U *at(int s, int idx) const {
-        return ptr<U>(s) + idx;
-    }
-};
-
 // Per-thread neighbour offsets: element index of (x+dx, y+dy, z+dz) is
 // X[dx+1] + Y[dy+1] + Z[dz+1] (X includes the cell's own index).
 struct Nb3 {
