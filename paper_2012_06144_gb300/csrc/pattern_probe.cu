@@ -14,6 +14,9 @@
 //   copy     float4 copy of half the planes into the other half (a STREAM copy)
 //   local    read and write every plane at the cell
 //   aa_mix   21 planes local, 21 read at x - e and written at x + e (the fused step)
+//   aa_xalign as aa_mix, but the 21 swapped planes written at (x, y + e_y, z + e_z):
+//            the same lines a block-aligned (cluster-exchanged) write of the
+//            swapped step would produce, without the x misalignment
 //   aa_odd   every plane read at x - e and written at x + e
 //   pull     read at x - e, write at the cell (two grids)
 //   push     read at the cell, write at x + e (two grids)
@@ -31,7 +34,7 @@ namespace {
 
 constexpr int Q = 42, BX = 32, BY = 2, BZ = 4;
 
-enum Pattern { LOCAL, AA_MIX, AA_ODD, PULL, PUSH, TWIST };
+enum Pattern { LOCAL, AA_MIX, AA_XALIGN, AA_ODD, PULL, PUSH, TWIST };
 
 __device__ __forceinline__ int3 direction(int s) {
     const int d = s % 27;
@@ -46,6 +49,7 @@ __device__ __forceinline__ void shifts(int s, int3 &r, int3 &w) {
     const int3 t = make_int3(max(e.x, 0), max(e.y, 0), max(e.z, 0));
     r = w = z;
     if (P == AA_MIX && s >= Q / 2) { r = m; w = e; }
+    if (P == AA_XALIGN && s >= Q / 2) { r = m; w = make_int3(0, e.y, e.z); }
     if (P == AA_ODD) { r = m; w = e; }
     if (P == PULL) r = m;
     if (P == PUSH) w = e;
@@ -127,6 +131,7 @@ int main(int argc, char **argv) {
                                  2.0 * half4 * sizeof(float4), iters);
     const double local = time_gbs([&] { move<LOCAL><<<grid, block>>>(f, o, n, N); }, bytes, iters);
     const double aa_mix = time_gbs([&] { move<AA_MIX><<<grid, block>>>(f, o, n, N); }, bytes, iters);
+    const double aa_xalign = time_gbs([&] { move<AA_XALIGN><<<grid, block>>>(f, o, n, N); }, bytes, iters);
     const double aa_odd = time_gbs([&] { move<AA_ODD><<<grid, block>>>(f, o, n, N); }, bytes, iters);
     const double pull = time_gbs([&] { move<PULL><<<grid, block>>>(f, o, n, N); }, bytes, iters);
     const double push = time_gbs([&] { move<PUSH><<<grid, block>>>(f, o, n, N); }, bytes, iters);
@@ -136,7 +141,8 @@ int main(int argc, char **argv) {
     cudaFree(o);
     if (!ok) return 1;
     std::printf("{\"n\": %d, \"planes\": %d, \"iters\": %d, \"unit\": \"GB/s\", \"copy\": %.1f, \"local\": %.1f, "
-                "\"aa_mix\": %.1f, \"aa_odd\": %.1f, \"pull\": %.1f, \"push\": %.1f, \"twist\": %.1f}\n",
-                n, Q, iters, copy, local, aa_mix, aa_odd, pull, push, twist);
+                "\"aa_mix\": %.1f, \"aa_xalign\": %.1f, \"aa_odd\": %.1f, \"pull\": %.1f, \"push\": %.1f, "
+                "\"twist\": %.1f}\n",
+                n, Q, iters, copy, local, aa_mix, aa_xalign, aa_odd, pull, push, twist);
     return 0;
 }

@@ -15,5 +15,5 @@ def test_pattern_probe_reports_every_pattern():
     assert r.returncode == 0, r.stderr
     out = json.loads(r.stdout.strip().splitlines()[-1])
     assert out["n"] == 128 and out["planes"] == 42 and out["unit"] == "GB/s"
-    for k in ("copy", "local", "aa_mix", "aa_odd", "pull", "push", "twist"):
+    for k in ("copy", "local", "aa_mix", "aa_xalign", "aa_odd", "pull", "push", "twist"):
         assert 0.0 < out[k] < 20000.0, (k, out[k])
