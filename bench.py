@@ -51,6 +51,12 @@ def bytes_per_cell(q: int, precision: str = "fp32") -> int:
 FALLBACK_HBM_GBS = 6800.0
 
 
+def roofline_mlups(peak_gbs: float, bytes_per_cell_: float) -> float:
+    """The memory-bound ceiling of a step (Section 5.1, eq:roofline): the copy
+    bandwidth divided by the bytes moved per cell, in MLUPS."""
+    return peak_gbs * 1e3 / bytes_per_cell_
+
+
 def env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -589,6 +595,7 @@ def main():
     algo_bytes = N * bytes_per_cell(q, args.precision)
     achieved = algo_bytes / (launch_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "roof_mlups": roofline_mlups(peak, bytes_per_cell(q, args.precision)),
             "traffic": recorded_traffic(args.workload, N) if args.precision == "fp32" else None, "peak_kind": peak_kind,
             "kernel": f"fused_step_kernel<{args.precision}, 27>", "algorithmic_bytes_per_cell": bytes_per_cell(q, args.precision),
             "launch_ms": launch_ms}

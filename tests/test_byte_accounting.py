@@ -59,3 +59,32 @@ def test_fused_design_moves_less_than_the_paper_design():
     assert bench.bytes_per_cell(27, "fp32") == 344
     assert (pl + ps + hl + hs) * 4 == 384  # u written and read back, phi read twice
     assert bench.bytes_per_cell(27, "fp16") == 184
+
+
+def _tables():
+    rows = []
+    with open(os.path.join(HERE, "golden", "roofline_tables.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                gpu, kernel, *v = line.split()
+                rows.append((gpu, kernel, *map(float, v)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _tables(), ids=lambda r: f"{r[0]}-{r[1]}")
+def test_roofline_arithmetic_reproduces_the_papers_tables(row):
+    """The benchmark's ceiling (copy bandwidth / bytes per cell) gives the paper's
+    kernel estimates, and measured / estimate its printed ratios, to the printed
+    digits; the balances follow B_c = n_b / n_f, B_m = b_s / p_peak, l = min(1, B_m / B_c)."""
+    gpu, kernel, b_s, p_peak, n_b, n_f, B_c, B_m, l, est, meas, ratio = row
+    ceiling = bench.roofline_mlups(b_s, n_b) / 1e3  # GLUPs
+    assert abs(ceiling - est) <= 0.005 + 1e-12
+    assert abs(100.0 * meas / ceiling - ratio) < 1.0  # printed as whole percent (truncated or rounded)
+    assert abs(n_b / n_f - B_c) <= 0.005 + 1e-12
+    assert abs(b_s / (p_peak * 1e3) - B_m) <= 0.005 + 1e-12
+    assert abs(min(1.0, (b_s / (p_peak * 1e3)) / (n_b / n_f)) - l) <= 0.012  # the table divides the rounded balances
+
+
+def test_benchmark_ceiling_of_the_fused_step():
+    # 344 B per cell at the measured 6770.5 GB/s copy bandwidth
+    assert bench.roofline_mlups(6770.5, 344) == pytest.approx(19681.7, abs=0.1)
