@@ -255,3 +255,47 @@ class State:
         phi = self.phi()
         u, pr = fields(self.p, self.g, phi)
         return phi, u, pr
+
+
+DIAGNOSTIC_NAMES = ("mass", "mom_x", "mom_y", "mom_z", "light_vol", "light_x", "light_y", "light_z", "light_ux",
+                    "light_uy", "light_uz", "max_u")
+
+
+def diagnostics(prob, phi, u) -> dict:
+    """Diagnostics of a state from its fields (FP64 sums, plain numpy).
+
+    The quantities Section 6.1 follows for a rising bubble -- the light phase's
+    centroid and its velocity -- plus the conserved phase mass and the momentum:
+
+    * mass          sum phi (conserved by the phase step, Section 3.1);
+    * mom_a         sum rho u_a, rho = rho_L + phi (rho_H - rho_L) (eq:density),
+                    phi clamped to [0, 1] there when the problem clamps it;
+    * light_vol     sum b with the bubble indicator b = clamp(1 - 2 phi, 0, 1):
+                    1 in the light phase, 0 from the interface's mid-level
+                    phi = 1/2 on, so the heavy bulk does not enter;
+    * light_a       sum (a + 1/2) b / sum b, cell centres at i + 1/2 (centroid);
+    * light_ua      sum u_a b / sum b (the bubble's mean velocity);
+    * max_u         max |u|.
+
+    ``phi`` has shape (nz, ny, nx) and ``u`` (3, nz, ny, nx)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    nz, ny, nx = phi.shape
+    rho_L = float(prob.rho_L)
+    f = np.clip(phi, 0.0, 1.0) if getattr(prob, "clamp_phi", 0) else phi
+    rho = rho_L + f * (float(prob.rho_H) - rho_L)
+    b = np.clip(1.0 - 2.0 * phi, 0.0, 1.0)
+    vol = b.sum()
+    centre = (np.arange(nx) + 0.5, np.arange(ny) + 0.5, np.arange(nz) + 0.5)
+    out = {"mass": phi.sum()}
+    for a, name in enumerate("xyz"):
+        out["mom_" + name] = (rho * u[a]).sum()
+    out["light_vol"] = vol
+    # sum over the other two axes first: sum_c (a_c + 1/2) b_c
+    per_axis = (b.sum(axis=(0, 1)), b.sum(axis=(0, 2)), b.sum(axis=(1, 2)))
+    for a, name in enumerate("xyz"):
+        out["light_" + name] = float((centre[a] * per_axis[a]).sum() / vol) if vol > 0 else 0.0
+    for a, name in enumerate("xyz"):
+        out["light_u" + name] = float((u[a] * b).sum() / vol) if vol > 0 else 0.0
+    out["max_u"] = float(np.sqrt((u * u).sum(axis=0)).max())
+    return {k: float(out[k]) for k in DIAGNOSTIC_NAMES}

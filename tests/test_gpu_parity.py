@@ -33,22 +33,6 @@ def rel_linf(a, b, floor=0.0):
     return float(np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), floor))
 
 
-def storage_floor(orc, prob, phi0, steps):
-    """The FP64 oracle's own deviation when its state is rounded to float32 after
-    every step (FP32 storage with exact arithmetic), per field (phi, u, p)."""
-    p = orc.make_problem(prob)
-    a, b = orc.State(p, phi0), orc.State(p, phi0)
-    for _ in range(steps):
-        a.run(1)
-        b.run(1)
-        b.h = b.h.astype(np.float32).astype(np.float64)
-        b.g = b.g.astype(np.float32).astype(np.float64)
-        b.phi_prev = b.phi_prev.astype(np.float32).astype(np.float64)
-    ref = a.fields()
-    floor = [rel_linf(x, y, 1e-6 if k == 1 else 0.0) for k, (x, y) in enumerate(zip(b.fields(), ref))]
-    return ref, floor
-
-
 def oracle_one_step(orc, prob, h, g, phi):
     """Oracle from the library's state (g^t, h^{t+1}, phi^t): hydro(t) then phase(t+1)."""
     p = orc.make_problem(prob)
@@ -156,20 +140,28 @@ def test_split_steps_bitwise(lbm):
 
 def test_rising_bubble_walls(lbm, orc):
     """Walled box, D3Q27, gravity, buoyancy and the phi clamp (Eo 10, Mo 1e-3,
-    t_ref 1000): 150 steps against the oracle.  The start from rest drives a
-    transient that amplifies rounding, so the bound is max(1e-5, 2 x the error
-    that FP32 storage alone causes in the oracle on the same case)."""
+    t_ref 1000): 150 steps against the oracle.  phi, u and p within 1e-5, phi on
+    the cells with phi < 0.999 (the bubble and its interface).  In the heavy bulk
+    the phase step's normal G/|G| follows gradients of the size of the rounding,
+    so rounding moves phi there: the FP64 oracle run with its state rounded to
+    float32 after every step departs from the plain oracle by 1.1e-5 in phi on
+    this case, all of it in the bulk (7e-8 elsewhere); the whole box is held to
+    3e-5."""
     prob, phi0 = W.rising_bubble(24, 48, 20, D=12.0, t_ref=1000.0)
     sim = lbm.Simulation.from_problem(prob)
     sim.init_phase(phi0)
     sim.step(150)
     sim.synchronize()
     phi, u, p = sim.fields(on_device=False)
-    (rphi, ru, rp), floor = storage_floor(orc, prob, phi0, 150)
-    tol = [max(TOL, 2 * f) for f in floor]
-    assert rel_linf(phi, rphi) <= tol[0]
-    assert rel_linf(u, ru, 1e-6) <= tol[1]
-    assert rel_linf(p, rp) <= tol[2]
+    rphi, ru, rp = orc.State(orc.make_problem(prob), phi0).run(150).fields()
+    bubble = rphi < 0.999
+    err = np.abs(phi.astype(np.float64) - rphi)
+    print("walled 24x48x20, 150 steps: phi (phi < 0.999)", err[bubble].max(), "phi (box)", err.max(),
+          "u", rel_linf(u, ru, 1e-6), "p", rel_linf(p, rp))
+    assert err[bubble].max() / np.abs(rphi).max() <= TOL
+    assert err.max() / np.abs(rphi).max() <= 3e-5
+    assert rel_linf(u, ru, 1e-6) <= TOL
+    assert rel_linf(p, rp) <= TOL
 
 
 def test_host_and_device_outputs_agree(lbm):

@@ -94,38 +94,56 @@ def test_mass_kept_with_16bit_storage(lbm, prec):
     assert abs(sim.reduce()["mass"] - m0) <= 1e-6 * m0
 
 
-def _rise(phi, u):
-    lf = 1.0 - phi
-    return float((u[1] * lf).sum() / lf.sum())
-
-
 def test_precision_bubble_errors(lbm, orc):
     """64^3 walled rising bubble (D = 16, Eo 10, Mo 1e-3, t_ref 1000), 1000 steps:
-    phi L-infinity, rise velocity and mass drift of each storage format against
-    the FP64 oracle."""
+    phi L-infinity (whole box and the cells with phi < 0.999), the bubble's
+    centroid and rise velocity (lbm_reduce, indicator clamp(1 - 2 phi, 0, 1))
+    and the mass drift of each storage format against the FP64 oracle.  With
+    LBM_PRECISION_RECORD set to a path, the measured errors are written there as
+    JSON (the record the benchmark quotes)."""
+    import json
+    import os
+
+    import bench
+
     prob, phi0 = W.precision_bubble()
     steps = 1000
     ref = orc.State(orc.make_problem(prob), phi0).run(steps)
     rphi, ru, _ = ref.fields()
-    r_rise = _rise(rphi, ru)
-    m_ref = rphi.sum()
+    rd = orc.diagnostics(prob, rphi, ru)
+    m0 = float(phi0.astype(np.float64).sum())
+    bubble = rphi < 0.999
     errs = {}
     for prec in ("fp32", "fp16", "bf16"):
         sim = lbm.Simulation.from_problem(prob, precision=prec)
         sim.init_phase(phi0)
         sim.step(steps)
         sim.synchronize()
-        phi, u, _ = (t.cpu().numpy().astype(np.float64) for t in sim.fields())
+        d = sim.reduce()
+        phi = sim.fields()[0].cpu().numpy().astype(np.float64)
         errs[prec] = dict(phi_linf=float(np.abs(phi - rphi).max()),
-                          rise_rel=abs(_rise(phi, u) - r_rise) / abs(r_rise),
-                          mass_drift=abs(phi.sum() - m_ref) / m_ref)
+                          phi_linf_bubble=float(np.abs(phi - rphi)[bubble].max()),
+                          centroid_y_abs=abs(d["light_y"] - rd["light_y"]),
+                          centroid_abs=float(np.linalg.norm([d["light_" + a] - rd["light_" + a] for a in "xyz"])),
+                          rise_velocity_rel=abs(d["light_uy"] - rd["light_uy"]) / abs(rd["light_uy"]),
+                          mass_drift=abs(d["mass"] - m0) / m0)
         sim.close()
-    print("precision errors vs FP64 oracle:", errs, "rise velocity", r_rise)
-    # stated accuracy (64^3, 1000 steps; measured on a GB300: FP32 phi 5.6e-4,
-    # rise 3.3e-6; FP16 4.2e-4, 1.3e-4; BF16 2.7e-3, 4.5e-3 -- the start from rest
-    # amplifies rounding, so FP32 and FP16 are close in phi)
-    assert errs["fp32"]["phi_linf"] <= 2e-3 and errs["fp32"]["rise_rel"] <= 1e-4
-    assert errs["fp16"]["phi_linf"] <= 2e-3 and errs["fp16"]["rise_rel"] <= 1e-3
-    assert errs["bf16"]["phi_linf"] <= 1e-2 and errs["bf16"]["rise_rel"] <= 2e-2
+    print("precision errors vs FP64 oracle:", errs, "oracle centroid", rd["light_y"], "rise velocity", rd["light_uy"])
+    path = os.environ.get("LBM_PRECISION_RECORD")
+    if path:
+        rec = {"case": "64^3 walled rising bubble, D = 16 at (32, 16, 32), Eo 10, Mo 1e-3, t_ref 1000, density "
+                       "ratio 1000, D3Q15+D3Q27, 1000 steps, vs the FP64 oracle",
+               "source_hash": bench.kernel_source_hash(), "oracle_centroid_y": rd["light_y"],
+               "oracle_rise_velocity": rd["light_uy"], "errors": errs}
+        with open(path, "w") as f:
+            json.dump(rec, f, indent=1)
+    # stated accuracy (64^3, 1000 steps; the start from rest amplifies rounding,
+    # and phi in the heavy bulk follows the rounding of near-zero gradients, so
+    # FP32 and FP16 are close in phi over the whole box)
+    assert errs["fp32"]["phi_linf"] <= 2e-3 and errs["fp32"]["rise_velocity_rel"] <= 1e-4
+    assert errs["fp16"]["phi_linf"] <= 2e-3 and errs["fp16"]["rise_velocity_rel"] <= 1e-3
+    assert errs["bf16"]["phi_linf"] <= 1e-2 and errs["bf16"]["rise_velocity_rel"] <= 2e-2
+    assert errs["fp32"]["centroid_abs"] <= 1e-3 and errs["fp16"]["centroid_abs"] <= 1e-2
+    assert errs["bf16"]["centroid_abs"] <= 1e-1
     for e in errs.values():
         assert e["mass_drift"] <= 1e-6
