@@ -14,15 +14,6 @@
 //   copy     float4 copy of half the planes into the other half (a STREAM copy)
 //   local    read and write every plane at the cell
 //   aa_mix   21 planes local, 21 read at x - e and written at x + e (the fused step)
-//   aa_xalign as aa_mix, but the 21 swapped planes written at (x, y + e_y, z + e_z):
-//            the same lines a block-aligned (cluster-exchanged) write of the
-//            swapped step would produce, without the x misalignment
-//   aa_cluster as aa_mix, with the swapped planes whose e_x = +-1 staged in shared
-//            memory and written as whole lines after a barrier of an 8-block
-//            cluster along x: lane 0 (or 31) takes the neighbour block's element
-//            through distributed shared memory; at a cluster's edge that one
-//            element is written by its own thread (-1 if nx / 32 is not a
-//            multiple of 8)
 //   aa_odd   every plane read at x - e and written at x + e
 //   pull     read at x - e, write at the cell (two grids)
 //   push     read at the cell, write at x + e (two grids)
@@ -31,7 +22,6 @@
 // of two and a multiple of 32.  Two buffers of 42 n^3 floats (45 GB at n = 512).
 //
 // Usage: pattern_probe [n=512] [iters=20]
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -41,7 +31,7 @@ namespace {
 
 constexpr int Q = 42, BX = 32, BY = 2, BZ = 4;
 
-enum Pattern { LOCAL, AA_MIX, AA_XALIGN, AA_ODD, PULL, PUSH, TWIST };
+enum Pattern { LOCAL, AA_MIX, AA_ODD, PULL, PUSH, TWIST };
 
 __device__ __forceinline__ int3 direction(int s) {
     const int d = s % 27;
@@ -56,7 +46,6 @@ __device__ __forceinline__ void shifts(int s, int3 &r, int3 &w) {
     const int3 t = make_int3(max(e.x, 0), max(e.y, 0), max(e.z, 0));
     r = w = z;
     if (P == AA_MIX && s >= Q / 2) { r = m; w = e; }
-    if (P == AA_XALIGN && s >= Q / 2) { r = m; w = make_int3(0, e.y, e.z); }
     if (P == AA_ODD) { r = m; w = e; }
     if (P == PULL) r = m;
     if (P == PUSH) w = e;
@@ -84,89 +73,6 @@ __global__ void __launch_bounds__(BX *BY *BZ, 4) move(const float *__restrict__ 
         const size_t c = (size_t)((x + w.x) & m) + (size_t)n * (((y + w.y) & m) + (size_t)n * ((z + w.z) & m));
         o[s * N + c] = v[s] * 1.0000001f;
     }
-}
-
-// The aa_mix pattern with cluster-aligned writes of the x-shifted swapped planes.
-constexpr int kCluster = 8;
-constexpr int kShifted = 14;  // swapped planes s = 21..41 whose direction s mod 27 has e_x != 0
-
-__host__ __device__ constexpr int shifted_slot(int s) {  // index among the staged planes, or -1
-    int k = 0;
-    for (int t = Q / 2; t < Q; ++t) {
-        const int d = t % 27;
-        if (d % 3 - 1 != 0) {
-            if (t == s) return k;
-            ++k;
-        }
-    }
-    return -1;
-}
-static_assert(shifted_slot(Q - 1) == kShifted - 1 || shifted_slot(Q - 2) == kShifted - 1, "staged plane count");
-
-__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(BX *BY *BZ, 4)
-    move_cluster(const float *__restrict__ f, float *__restrict__ o, int n, unsigned long long N) {
-    namespace cg = cooperative_groups;
-    __shared__ float stage[kShifted][BY * BZ][BX];
-    cg::cluster_group cluster = cg::this_cluster();
-    const int nbx = n / BX, m = n - 1;
-    const int by = blockIdx.x / nbx, bx = blockIdx.x - by * nbx;
-    const int tx = threadIdx.x, row = threadIdx.y + BY * threadIdx.z;
-    const int x = bx * BX + tx, y = by * BY + threadIdx.y, z = blockIdx.y * BZ + threadIdx.z;
-    const unsigned rank = cluster.block_rank();
-    float v[Q];
-#pragma unroll
-    for (int s = 0; s < Q; ++s) {
-        int3 r, w;
-        shifts<AA_MIX>(s, r, w);
-        const size_t c = (size_t)((x + r.x) & m) + (size_t)n * (((y + r.y) & m) + (size_t)n * ((z + r.z) & m));
-        v[s] = __ldg(f + s * N + c);
-    }
-#pragma unroll
-    for (int s = 0; s < Q; ++s) {
-        int3 r, w;
-        shifts<AA_MIX>(s, r, w);
-        const float val = v[s] * 1.0000001f;
-        if (shifted_slot(s) >= 0) {
-            stage[shifted_slot(s)][row][tx] = val;
-            // the element that crosses into the next cluster: written by its own thread
-            const bool edge = w.x > 0 ? (rank == kCluster - 1 && tx == BX - 1) : (rank == 0 && tx == 0);
-            if (edge) {
-                const size_t c = (size_t)((x + w.x) & m) + (size_t)n * (((y + w.y) & m) + (size_t)n * ((z + w.z) & m));
-                o[s * N + c] = val;
-            }
-        } else {
-            const size_t c = (size_t)((x + w.x) & m) + (size_t)n * (((y + w.y) & m) + (size_t)n * ((z + w.z) & m));
-            o[s * N + c] = val;
-        }
-    }
-    cluster.sync();
-    const float *left = cluster.map_shared_rank(&stage[0][0][0], rank > 0 ? rank - 1 : rank);
-    const float *right = cluster.map_shared_rank(&stage[0][0][0], rank < kCluster - 1 ? rank + 1 : rank);
-#pragma unroll
-    for (int s = Q / 2; s < Q; ++s) {
-        const int k = shifted_slot(s);
-        if (k < 0) continue;
-        int3 r, w;
-        shifts<AA_MIX>(s, r, w);
-        // whole line [x0, x0 + 32) of row (y + e_y, z + e_z): position x takes the value
-        // produced at x - e_x
-        float val;
-        bool have = true;
-        if (w.x > 0) {
-            if (tx > 0) val = stage[k][row][tx - 1];
-            else if (rank > 0) val = left[(k * BY * BZ + row) * BX + BX - 1];
-            else have = false;
-        } else {
-            if (tx < BX - 1) val = stage[k][row][tx + 1];
-            else if (rank < kCluster - 1) val = right[(k * BY * BZ + row) * BX];
-            else have = false;
-        }
-        if (have) {
-            const size_t c = (size_t)(x & m) + (size_t)n * (((y + w.y) & m) + (size_t)n * ((z + w.z) & m));
-            o[s * N + c] = val;
-        }
-    }
-    cluster.sync();  // neighbours have read this block's stage
 }
 
 __global__ void copy4(const float4 *__restrict__ a, float4 *__restrict__ b, size_t n4) {
@@ -221,10 +127,6 @@ int main(int argc, char **argv) {
                                  2.0 * half4 * sizeof(float4), iters);
     const double local = time_gbs([&] { move<LOCAL><<<grid, block>>>(f, o, n, N); }, bytes, iters);
     const double aa_mix = time_gbs([&] { move<AA_MIX><<<grid, block>>>(f, o, n, N); }, bytes, iters);
-    const double aa_xalign = time_gbs([&] { move<AA_XALIGN><<<grid, block>>>(f, o, n, N); }, bytes, iters);
-    const double aa_cluster = (n / BX) % kCluster == 0
-                                  ? time_gbs([&] { move_cluster<<<grid, block>>>(f, o, n, N); }, bytes, iters)
-                                  : -1.0;
     const double aa_odd = time_gbs([&] { move<AA_ODD><<<grid, block>>>(f, o, n, N); }, bytes, iters);
     const double pull = time_gbs([&] { move<PULL><<<grid, block>>>(f, o, n, N); }, bytes, iters);
     const double push = time_gbs([&] { move<PUSH><<<grid, block>>>(f, o, n, N); }, bytes, iters);
@@ -234,8 +136,7 @@ int main(int argc, char **argv) {
     cudaFree(o);
     if (!ok) return 1;
     std::printf("{\"n\": %d, \"planes\": %d, \"iters\": %d, \"unit\": \"GB/s\", \"copy\": %.1f, \"local\": %.1f, "
-                "\"aa_mix\": %.1f, \"aa_xalign\": %.1f, \"aa_cluster\": %.1f, \"aa_odd\": %.1f, \"pull\": %.1f, "
-                "\"push\": %.1f, \"twist\": %.1f}\n",
-                n, Q, iters, copy, local, aa_mix, aa_xalign, aa_cluster, aa_odd, pull, push, twist);
+                "\"aa_mix\": %.1f, \"aa_odd\": %.1f, \"pull\": %.1f, \"push\": %.1f, \"twist\": %.1f}\n",
+                n, Q, iters, copy, local, aa_mix, aa_odd, pull, push, twist);
     return 0;
 }

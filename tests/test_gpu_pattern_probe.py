@@ -15,5 +15,6 @@ def test_pattern_probe_reports_every_pattern():
     assert r.returncode == 0, r.stderr
     out = json.loads(r.stdout.strip().splitlines()[-1])
     assert out["n"] == 128 and out["planes"] == 42 and out["unit"] == "GB/s"
-    for k in ("copy", "local", "aa_mix", "aa_xalign", "aa_odd", "pull", "push", "twist"):
+    assert "aa_cluster" not in out and "aa_xalign" not in out
+    for k in ("copy", "local", "aa_mix", "aa_odd", "pull", "push", "twist"):
         assert 0.0 < out[k] < 20000.0, (k, out[k])
