@@ -67,25 +67,22 @@ constexpr int kNumShapes = 3;
 constexpr int kNumOrders = 2;  // 0: member after member, 1: members interleaved tile by tile
 constexpr int kNumHalos = 2;   // 0: per-thread loads, 1: TMA copy (per-thread loads on periodic faces)
 
-// One block per entry tiles[blockIdx.x] = (member within the group, bx, by, bz).
+// One tile (member within the group, bx, by, bz) = e of the table.
 template <int QG, bool G_SW, bool H_SW, int TY, int TZ, int HALO>
-__global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
-    batch_step_kernel(const __grid_constant__ GroupArgs a, const int4 *__restrict__ tiles, int cur) {
+__device__ __forceinline__ void batch_tile(const GroupArgs &a, const int4 e, int cur,
+                                           float (*tile)[TY + 2][HALO ? kTmaRow : TX + 2], uint64_t *bar) {
     constexpr int HW = HALO ? kTmaRow : TX + 2;
-    __shared__ __align__(128) float tile[TZ + 2][TY + 2][HW];
-    __shared__ uint64_t bar;
-    const int4 e = tiles[blockIdx.x];
     const MemberDesc &d = a.m[e.x];
     const BaseLat32<float> lh{d.h_rest, d.h_mov, (unsigned)d.p.N}, lg{d.g_rest, d.g_mov, (unsigned)d.p.N};
-    const HaloTma t{&bar, d.flag + 1};
+    const HaloTma t{bar, d.flag + 1};
     const HaloTma *tma = nullptr;
     if (HALO && tma_halo_fits<TY, TZ>(d.p, e.y, e.z, e.w)) {  // block-uniform
         const bool lead = threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
-        if (lead) tma_bar_init(&bar);
+        if (lead) tma_bar_init(bar);
         __syncthreads();
         if (lead)
-            tma_load_tile(&tile[0][0][0], &a.phi_map[e.x][cur], e.y * TX - 4, e.z * TY - 1, e.w * TZ - 1, &bar,
-                          (unsigned)sizeof(tile));
+            tma_load_tile(&tile[0][0][0], &a.phi_map[e.x][cur], e.y * TX - 4, e.z * TY - 1, e.w * TZ - 1, bar,
+                          (unsigned)(sizeof(float) * (TZ + 2) * (TY + 2) * HW));
         tma = &t;
     }
     tile_update<float, QG, 15, G_SW, H_SW, true, false, TY, TZ, true, HW>(d.p, lh, lg, d.phi[cur], d.phi[cur ^ 1],
@@ -93,13 +90,57 @@ __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
                                                                          threadIdx.y, threadIdx.z, tma);
 }
 
+#ifndef LBM_BATCH_PERSISTENT
+#define LBM_BATCH_PERSISTENT 0
+#endif
+
+#if LBM_BATCH_PERSISTENT
+// Measurement variant (built with -DLBM_BATCH_PERSISTENT=1, per-thread halo loads
+// only): a persistent grid whose blocks walk the table with a stride of the grid
+// size, the tile body behind a call so that the loop leaves its register
+// allocation alone.
+template <int QG, bool G_SW, bool H_SW, int TY, int TZ>
+__device__ __noinline__ void batch_tile_call(const GroupArgs &a, const int4 e, int cur, float (*tile)[TY + 2][TX + 2]) {
+    batch_tile<QG, G_SW, H_SW, TY, TZ, 0>(a, e, cur, tile, nullptr);
+}
+
+template <int QG, bool G_SW, bool H_SW, int TY, int TZ, int HALO>
+__global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
+    batch_step_kernel(const __grid_constant__ GroupArgs a, const int4 *__restrict__ tiles, int cur, int ntiles) {
+    __shared__ __align__(128) float tile[TZ + 2][TY + 2][TX + 2];
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        batch_tile_call<QG, G_SW, H_SW, TY, TZ>(a, tiles[k], cur, tile);
+        __syncthreads();  // every thread is done with this tile's phi before the next fill
+    }
+}
+#else
+// One block per entry tiles[blockIdx.x] = (member within the group, bx, by, bz).
+template <int QG, bool G_SW, bool H_SW, int TY, int TZ, int HALO>
+__global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
+    batch_step_kernel(const __grid_constant__ GroupArgs a, const int4 *__restrict__ tiles, int cur, int ntiles) {
+    constexpr int HW = HALO ? kTmaRow : TX + 2;
+    __shared__ __align__(128) float tile[TZ + 2][TY + 2][HW];
+    __shared__ uint64_t bar;
+    batch_tile<QG, G_SW, H_SW, TY, TZ, HALO>(a, tiles[blockIdx.x], cur, tile, &bar);
+}
+#endif
+
 template <int QG, bool G_SW, bool H_SW, int TY, int TZ>
 static cudaError_t launch_shape(int halo, const GroupArgs &a, const int4 *tiles, int ntiles, int cur,
                                 cudaStream_t st) {
+#if LBM_BATCH_PERSISTENT
+    if (halo) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(ntiles, sms * LBM_MIN_BLOCKS);
+    batch_step_kernel<QG, G_SW, H_SW, TY, TZ, 0><<<grid, dim3(TX, TY, TZ), 0, st>>>(a, tiles, cur, ntiles);
+#else
     if (halo)
-        batch_step_kernel<QG, G_SW, H_SW, TY, TZ, 1><<<ntiles, dim3(TX, TY, TZ), 0, st>>>(a, tiles, cur);
+        batch_step_kernel<QG, G_SW, H_SW, TY, TZ, 1><<<ntiles, dim3(TX, TY, TZ), 0, st>>>(a, tiles, cur, ntiles);
     else
-        batch_step_kernel<QG, G_SW, H_SW, TY, TZ, 0><<<ntiles, dim3(TX, TY, TZ), 0, st>>>(a, tiles, cur);
+        batch_step_kernel<QG, G_SW, H_SW, TY, TZ, 0><<<ntiles, dim3(TX, TY, TZ), 0, st>>>(a, tiles, cur, ntiles);
+#endif
     return cudaGetLastError();
 }
 
@@ -354,8 +395,9 @@ lbm_status lbm_batch_create(lbm_batch_t **out, int count, const lbm_domain *doms
             return lbm::set_thread_error("batched stepping supports FP32 storage only"), LBM_ERR_ARG;
         if (prms[i].phase_collision != LBM_PHASE_SRT)
             return lbm::set_thread_error("batched stepping supports the SRT phase collision only"), LBM_ERR_ARG;
-        if (prms[i].kernel_form != LBM_FORM_FUSED)
-            return lbm::set_thread_error("batched stepping runs the fused form only"), LBM_ERR_ARG;
+        if (prms[i].kernel_form != LBM_FORM_FUSED && prms[i].kernel_form != LBM_FORM_FUSED_CELL)
+            return lbm::set_thread_error("batched stepping runs the fused form (one cell per thread) only"),
+                   LBM_ERR_ARG;
         if (doms[i].q_phase != 15)
             return lbm::set_thread_error("batched stepping takes the D3Q15 phase-field lattice"), LBM_ERR_ARG;
         if (!lbm::offsets32(kp.N, doms[i].q_hydro, 15))
@@ -528,11 +570,18 @@ lbm_status lbm_batch_set_config(lbm_batch_t *b, int choice) {
     const int order = choice % lbm::kNumOrders, shape = (choice / lbm::kNumOrders) % lbm::kNumShapes,
               halo = choice / (lbm::kNumOrders * lbm::kNumShapes);
     BatchDeviceGuard dg(b->device);
-    const lbm_status st = build_table(b, shape, order);  // (re)encodes the tensor maps for the shape
+    static const char *no_tma =
+        "TMA halo staging unavailable (a member's nx is not a multiple of 4, or no driver support)";
+    if (halo == 1 && !b->tma_ok) return b->err = no_tma, LBM_ERR_STATE;  // refused before anything changes
+    lbm_status st = build_table(b, shape, order);  // (re)encodes the tensor maps for the shape
     if (st != LBM_OK) return st;
-    if (halo == 1 && !b->tma_ok)
-        return b->err = "TMA halo staging unavailable (a member's nx is not a multiple of 4, or no driver support)",
-               LBM_ERR_STATE;
+    if (halo == 1 && !b->tma_ok) {
+        // the tensor maps of this shape could not be encoded: the table goes back to
+        // the configuration in use, so that the next step launches a matching kernel
+        st = build_table(b, b->shape, b->order);
+        if (st != LBM_OK) return st;
+        return b->err = no_tma, LBM_ERR_STATE;
+    }
     if (b->halo != halo) drop_graphs(b);
     b->shape = shape;
     b->order = order;

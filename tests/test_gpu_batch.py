@@ -66,7 +66,9 @@ def _members(q):
 
 
 def _alone(lbm, prob, phi0, steps, what="state"):
-    sim = lbm.Simulation.from_problem(prob)
+    """The same problem stepped alone by the one-cell fused step, whose tile body
+    the batched kernel shares."""
+    sim = lbm.Simulation.from_problem(prob, form="cell")
     sim.init_phase(phi0)
     sim.step(steps)
     sim.synchronize()
@@ -149,6 +151,26 @@ def test_tuner_visits_every_candidate(lbm, orc, stream):
     batch.synchronize()
     for m, (prob, phi0) in zip(batch.members, members):
         _assert_as_close_as_single(orc, lbm, m, prob, phi0, 6 * 3 + 17)
+    batch.close()
+
+
+def test_refused_configuration_keeps_the_current_one(lbm, orc, stream):
+    """A configuration the batch refuses (TMA staging for members whose nx is not
+    a multiple of 4) leaves the one in use untouched: the tile table still
+    matches the kernel that the next step launches."""
+    members = _members(27)
+    batch = lbm.Batch.from_problems([p for p, _ in members], stream=stream)
+    for m, (_, phi0) in zip(batch.members, members):
+        m.init_phase(phi0)
+    batch.configure((2, 4), "round_robin", "loads")
+    with pytest.raises(lbm.LBMError) as e:
+        batch.configure((4, 2), "member", "tma")
+    assert e.value.status == lbm.LBM_ERR_STATE
+    batch.step(3)
+    batch.step(16)
+    batch.synchronize()
+    for m, (prob, phi0) in zip(batch.members, members):
+        _assert_as_close_as_single(orc, lbm, m, prob, phi0, 19)
     batch.close()
 
 
