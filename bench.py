@@ -45,9 +45,9 @@ UNIT = "MLUPS"
 STORE_BYTES = {"fp32": 4, "fp16": 2, "bf16": 2}
 
 
-def bytes_per_cell(q: int, precision: str = "fp32") -> int:
+def bytes_per_cell(q: int, precision: str = "fp32", q_phase: int = 15) -> int:
     b = STORE_BYTES[precision]
-    return (4 + 14 * b + 4 + (q - 1) * b) * 2 + 4 + 4
+    return (4 + (q_phase - 1) * b + 4 + (q - 1) * b) * 2 + 4 + 4
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -86,6 +86,31 @@ def workload(name: str, size: int = 512, generate: bool = True):
     raise ValueError(name)
 
 
+def apply_pair(args, prob, phi0, desc):
+    """The main step on another lattice pair of Section 5.1: the same box and
+    physics with D3Q{qp} + D3Q{q}, or (9+9) the two-dimensional box of as many
+    cells (16 size x 32 size x 1, circles of radius 12 on a pitch-64 lattice)."""
+    if args.pair == "15+27":
+        return prob, phi0, desc
+    qp, q = (int(v) for v in args.pair.split("+"))
+    if qp == 9:
+        prob, phi0 = W.roofline2d(16 * args.size, 32 * args.size)
+        return prob, phi0, (f"roofline2d: {prob.nx}x{prob.ny}x1 periodic, D2Q9+D2Q9, FP32, light circles R 12 on a "
+                            "pitch-64 lattice, rho ratio 1000, mu ratio 100, sigma 1e-4, xi 5, M 0.02, gravity Eo=10 at D=24")
+    prob.q_phase, prob.q_hydro = qp, q
+    return prob, phi0, desc.replace("D3Q15+D3Q27", f"D3Q{qp}+D3Q{q}")
+
+
+def step_kernel_name(args, prob) -> str:
+    """The kernel one step launches: the two-cells-per-thread fused step where it
+    applies and is chosen (every storage format by default: nx even, D3Q15 phase
+    lattice with D3Q19 / D3Q27 hydrodynamics), else the one-cell fused step."""
+    pair = (args.form in ("fused", "pair") and prob.nx % 2 == 0 and getattr(prob, "q_phase", 15) == 15
+            and prob.q_hydro in (19, 27))
+    name = "pair_step_kernel" if pair else "fused_step_kernel"
+    return f"{name}<{args.precision}, hydro D3Q{prob.q_hydro}, phase D3Q{getattr(prob, 'q_phase', 15)}>"
+
+
 def measured_hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -100,7 +125,7 @@ def kernel_source_hash() -> str:
     """Hash of the fused kernel's sources with comments and blank space removed
     (a change of comments leaves the recorded counters valid)."""
     h = hashlib.sha256()
-    for f in ("lbm_step.cu", "lbm_step_impl.cuh", "lbm_device.cuh"):
+    for f in ("lbm_step.cu", "lbm_pair.cu", "lbm_step_impl.cuh", "lbm_device.cuh", "lbm_internal.h"):
         with open(os.path.join(ROOT, "paper_2012_06144_gb300", "csrc", f)) as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -112,7 +137,7 @@ def kernel_source_hash() -> str:
 def recorded_traffic(workload_name: str, cells: int):
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
     only if it was taken on the current kernel source and the same box."""
-    path = os.path.join(ROOT, "profiles", "fused_step_kernel_roofline512_traffic.json")
+    path = os.path.join(ROOT, "profiles", "pair_step_kernel_roofline512_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
@@ -203,11 +228,13 @@ def cpu_baseline(seconds_budget: float = 20.0):
                       f"({prob.q_hydro}-velocity hydro lattice), FP64, OpenMP"}
 
 
-def run_config(args, desc, N, q, precision, world):
+def run_config(args, desc, N, q, precision, world, q_phase=15):
     """The `config` object of the JSON line (the same on both arms)."""
-    return {"workload": desc, "cells": N, "lattices": f"D3Q15+D3Q{q}",
+    lat = "D2Q9+D2Q9" if q_phase == 9 else f"D3Q{q_phase}+D3Q{q}"
+    return {"workload": desc, "cells": N, "lattices": lat,
             "storage": f"{precision} populations (FP32 rest), in-place AA",
-            "l2": f"state {N * (bytes_per_cell(q, precision) // 2) / 1e9:.1f} GB per GPU >> 129 MB L2, no flush needed",
+            "l2": f"state {N * (bytes_per_cell(q, precision, q_phase) // 2) / 1e9:.1f} GB per GPU >> 129 MB L2, "
+                  "no flush needed",
             "parallelism": f"replicas x{world}"}
 
 
@@ -256,24 +283,38 @@ def time_steps(sim, stream, steps: int) -> float:
     return a.elapsed_time(b)
 
 
-PRECISION_BOUNDS = {
-    "fp32": {"phi_linf": 2e-3, "rise_velocity_rel": 1e-4, "mass_drift": 1e-6},
-    "fp16": {"phi_linf": 2e-3, "rise_velocity_rel": 1e-3, "mass_drift": 1e-6},
-    "bf16": {"phi_linf": 1e-2, "rise_velocity_rel": 2e-2, "mass_drift": 1e-6},
-}
+def recorded_precision_errors():
+    """The storage formats' errors against the FP64 oracle, as measured by
+    tests/test_gpu_precision.py::test_precision_bubble_errors on a GB300 and
+    committed (64^3 walled rising bubble, 1000 steps); only if taken on the
+    current kernel source."""
+    path = os.path.join(ROOT, "profiles", "precision_errors_bubble64.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return {"record": None, "why": "no committed record"}
+    if rec.get("source_hash") != kernel_source_hash():
+        return {"record": None, "why": "recorded on another kernel source", "recorded_hash": rec.get("source_hash")}
+    return dict(rec, record="profiles/precision_errors_bubble64.json")
 
 
-def precision_forms(args, prob, phi0_dev, stream, peak):
-    """The FP16 and BF16 storage forms on the same workload and GPU (timing), with
-    the error each form is held to (phi L-infinity, rise velocity, mass drift
-    against the FP64 oracle on a 64^3 walled rising bubble after 1000 steps)."""
+def precision_forms(args, stream, peak):
+    """FP32, FP16 and BF16 population storage timed on one box and GPU: the
+    rising-bubble parameters on a 512^3 box walled on every face (D = 32 at
+    (256, 64, 256)), with each form's measured error against the FP64 oracle
+    (phi L-infinity, bubble centroid, rise velocity, mass drift on the 64^3
+    walled rising bubble after 1000 steps, from the committed record)."""
     import torch
 
     from paper_2012_06144_gb300 import lbm
 
-    out = {}
+    prob, phi0 = W.precision_timing(args.size)
+    phi0_dev = torch.from_numpy(phi0).cuda()
+    out = {"workload": f"{args.size}^3 walled rising bubble, D3Q15+D3Q27, D=32 at ({args.size // 2}, 64, "
+                       f"{args.size // 2}), Eo 10, Mo 1e-3, t_ref 2000, rho ratio 1000, mu ratio 100"}
     steps = min(args.steps, 500)
-    for prec in ("fp16", "bf16"):
+    for prec in ("fp32", "fp16", "bf16"):
         sim = lbm.Simulation.from_problem(prob, precision=prec, stream=stream)
         sim.init_phase(phi0_dev)
         sim.step(args.warmup)
@@ -286,13 +327,11 @@ def precision_forms(args, prob, phi0_dev, stream, peak):
         sim.close()
         del sim
         torch.cuda.empty_cache()
-    # The stated error of each storage form: the bounds that
-    # tests/test_gpu_precision.py::test_precision_bubble_errors asserts for the GPU
-    # against the FP64 oracle (64^3 walled rising bubble, 1000 steps); the oracle is
-    # run by the tests, not here.
-    out["stated_error"] = dict(PRECISION_BOUNDS, case="64^3 walled rising bubble D=16, Eo 10, Mo 1e-3, t_ref 1000, "
-                                                      "1000 steps, vs the FP64 oracle",
-                               verified_by="tests/test_gpu_precision.py::test_precision_bubble_errors")
+    out["fp16_speedup"] = out["fp32"]["ms_per_step"] / out["fp16"]["ms_per_step"]
+    out["bf16_speedup"] = out["fp32"]["ms_per_step"] / out["bf16"]["ms_per_step"]
+    out["measured_error"] = recorded_precision_errors()
+    del phi0_dev
+    torch.cuda.empty_cache()
     return out
 
 
@@ -305,12 +344,17 @@ def batched_form(args, stream, peak):
 
     from paper_2012_06144_gb300 import lbm
 
-    draws = W.batched()
+    draws = W.batched(count=args.batched_count)
     batch = lbm.Batch.from_problems([p for p, _, _ in draws], stream=stream)
     for m, (_, phi0, _) in zip(batch.members, draws):
         m.init_phase(phi0)
     cells = batch.cells
-    shape, order, halo, tune_ms = batch.tune(trial_steps=5)
+    if args.batched_config < 0:
+        shape, order, halo, tune_ms = batch.tune(trial_steps=5)
+    else:  # a fixed candidate, no tuning (profiling runs)
+        shape, order, halo = lbm.batch_candidate(args.batched_config)
+        batch.configure(shape, order, halo)
+        tune_ms = []
     batch.step(32)
     batch.synchronize()
     steps = args.batched_steps
@@ -342,7 +386,7 @@ def batched_form(args, stream, peak):
            "per_member_launches": {"value": cells / (solo_ms / 1e3) / 1e6, "ms_per_step": solo_ms,
                                    "steps": solo_steps},
            "gpu_launches_per_step": (len(batch) + 63) // 64,
-           "workload": "64 walled rising bubbles, sizes among 32^3, 48x96x48, 64x128x64, 96x192x96, D = nx/4 at "
+           "workload": f"{len(batch)} walled rising bubbles, sizes among 32^3, 48x96x48, 64x128x64, 96x192x96, D = nx/4 at "
                        "y = 2D, rho ratio 100/1000 (10 fails the s_nu bound), Eo ~ U[1,50], seed 6144"}
     batch.close()
     del batch
@@ -501,11 +545,18 @@ def main():
     ap.add_argument("--size", type=int, default=512, help="edge of the roofline box (512 = the benchmark)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="population storage format (arithmetic is FP32)")
+    ap.add_argument("--form", default="fused", choices=["fused", "cell", "pair"],
+                    help="fused-step variant of the main step (fused: the library's choice per storage format)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP16/BF16 storage forms")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched rising-bubble workload")
     ap.add_argument("--batched-steps", type=int, default=5000, help="timed steps of the batched workload")
+    ap.add_argument("--batched-count", type=int, default=64, help="members of the batched workload (64 = the benchmark)")
+    ap.add_argument("--batched-config", type=int, default=-1,
+                    help="tuner candidate of the batched workload (-1: autotune)")
+    ap.add_argument("--pair", default="15+27", choices=["15+27", "15+19", "19+19", "27+27", "19+27", "27+19", "9+9"],
+                    help="phase + hydrodynamic lattice of the main timed step (9+9: the 2-D box of as many cells)")
     ap.add_argument("--no-rising", action="store_true", help="skip the rising-bubble observables")
     ap.add_argument("--no-unfused", action="store_true", help="skip the unfused baseline")
     ap.add_argument("--no-pairs", action="store_true", help="skip the other stencil pairs")
@@ -540,10 +591,14 @@ def main():
     from paper_2012_06144_gb300 import lbm
 
     prob, phi0, desc = workload(args.workload, args.size)
+    prob, phi0, desc = apply_pair(args, prob, phi0, desc)
+    if args.pair != "15+27" and args.precision != "fp32":
+        raise SystemExit("other lattice pairs run with FP32 storage")
     N = prob.ncells
-    q = prob.q_hydro
+    q, qp = prob.q_hydro, prob.q_phase
+    headline = args.pair == "15+27" and args.precision == "fp32" and args.workload == "roofline" and args.form == "fused"
     stream = torch.cuda.Stream()
-    sim = lbm.Simulation.from_problem(prob, precision=args.precision, stream=stream)
+    sim = lbm.Simulation.from_problem(prob, precision=args.precision, form=args.form, stream=stream)
     phi0_dev = torch.from_numpy(phi0).cuda()
     torch.cuda.synchronize()
     sim.init_phase(phi0_dev)
@@ -592,32 +647,33 @@ def main():
                "mass_drift": float(diag[0] / float(phi0.astype(np.float64).sum()) - 1.0)}
 
     peak, peak_kind = measured_hbm_peak()
-    algo_bytes = N * bytes_per_cell(q, args.precision)
+    algo_bytes = N * bytes_per_cell(q, args.precision, qp)
     achieved = algo_bytes / (launch_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "roof_mlups": roofline_mlups(peak, bytes_per_cell(q, args.precision)),
-            "traffic": recorded_traffic(args.workload, N) if args.precision == "fp32" else None, "peak_kind": peak_kind,
-            "kernel": f"fused_step_kernel<{args.precision}, 27>", "algorithmic_bytes_per_cell": bytes_per_cell(q, args.precision),
+            "roof_mlups": roofline_mlups(peak, bytes_per_cell(q, args.precision, qp)),
+            "traffic": recorded_traffic(args.workload, N) if headline else None, "peak_kind": peak_kind,
+            "kernel": step_kernel_name(args, prob),
+            "algorithmic_bytes_per_cell": bytes_per_cell(q, args.precision, qp),
             "launch_ms": launch_ms}
 
     sim.close()
-    if rank == 0 and not args.no_pattern and args.precision == "fp32" and args.workload == "roofline":
+    if rank == 0 and not args.no_pattern and headline:
         torch.cuda.empty_cache()
         roof["pattern_ceiling"] = pattern_ceiling(args.size, achieved)
     forms = None
-    if rank == 0 and not args.no_precision and args.precision == "fp32" and args.workload == "roofline":
-        forms = precision_forms(args, prob, phi0_dev, stream, peak)
+    if rank == 0 and not args.no_precision and headline:
+        forms = precision_forms(args, stream, peak)
     batched = None
-    if rank == 0 and not args.no_batched and args.precision == "fp32" and args.workload == "roofline":
+    if rank == 0 and not args.no_batched and headline:
         batched = batched_form(args, stream, peak)
     unfused = None
-    if rank == 0 and not args.no_unfused and args.precision == "fp32" and args.workload == "roofline":
+    if rank == 0 and not args.no_unfused and headline:
         unfused = unfused_form(args, prob, phi0_dev, stream, peak, launch_ms)
     pairs = None
-    if rank == 0 and not args.no_pairs and args.precision == "fp32" and args.workload == "roofline":
+    if rank == 0 and not args.no_pairs and headline:
         pairs = stencil_pairs(args, prob, phi0_dev, stream, peak)
     rising = None
-    if rank == 0 and not args.no_rising and args.precision == "fp32" and args.workload == "roofline":
+    if rank == 0 and not args.no_rising and headline:
         rising = rising_bubble_form(args, stream)
 
     if rank == 0:
@@ -626,7 +682,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": run_config(args, desc, N, q, args.precision, world),
+            "config": run_config(args, desc, N, q, args.precision, world, qp),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
             "gpu_launches": args.steps, "precision_forms": forms, "batched_form": batched,
             "rising_bubble": rising, "unfused_form": unfused, "stencil_pairs": pairs,

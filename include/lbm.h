@@ -80,12 +80,21 @@ enum { LBM_PHASE_SRT = 0, LBM_PHASE_MRT = 1 };
 
 /* Kernel form of a time step.  FUSED: one kernel per step (Algorithm 2 with the
  * hydro(k-1) + phase(k) bracketing, in-place AA streaming, one copy of each
- * lattice: 344 B moved per cell at D3Q27).  UNFUSED: the passes of the paper's
- * straightforward Algorithm 1 -- a collision kernel for each lattice (storing u
- * and phi) and a streaming kernel for each, over two grids (708 B per cell at
- * D3Q27) -- computing the same update; the baseline the fused form is measured
- * against (Section 4.2).  UNFUSED needs FP32 storage and a single simulation. */
-enum { LBM_FORM_FUSED = 0, LBM_FORM_UNFUSED = 1 };
+ * lattice: 344 B moved per cell at D3Q27), in the variant the library measured
+ * faster for the storage format (FUSED_PAIR for FP16 and BF16 where it applies,
+ * FUSED_CELL otherwise).  UNFUSED: the passes of the paper's straightforward
+ * Algorithm 1 -- a collision kernel for each lattice (storing u and phi) and a
+ * streaming kernel for each, over two grids (708 B per cell at D3Q27) --
+ * computing the same update; the baseline the fused form is measured against
+ * (Section 4.2).  UNFUSED needs FP32 storage and a single simulation.
+ * FUSED_CELL: the fused step with one cell per thread.  FUSED_PAIR: the fused
+ * step with two neighbouring cells (x, x + 1) per thread, their arithmetic in
+ * packed FP32 pairs and their population pairs moved by one access where they
+ * are neighbours in memory; needs nx even, q_phase 15 with the SRT collision,
+ * q_hydro 19 or 27 and (q_hydro - 1) nx ny nz < 2^32.  All fused variants compute
+ * the same update; they differ in rounding only where a multiply and an add
+ * are fused differently. */
+enum { LBM_FORM_FUSED = 0, LBM_FORM_UNFUSED = 1, LBM_FORM_FUSED_CELL = 2, LBM_FORM_FUSED_PAIR = 3 };
 
 /* Box and lattices (Section 3; Section 5 uses D3Q15 for h and D3Q27 for g). */
 typedef struct {
@@ -122,7 +131,7 @@ typedef struct {
     double store_g_scale; /* 16-bit storage: power of two scaling g into the format's
                              normal range; 0 selects 4096 (FP16) or 1 (BF16)        */
     int phase_collision;  /* LBM_PHASE_SRT or LBM_PHASE_MRT                          */
-    int kernel_form;      /* LBM_FORM_FUSED or LBM_FORM_UNFUSED                      */
+    int kernel_form;      /* LBM_FORM_FUSED, _UNFUSED, _FUSED_CELL or _FUSED_PAIR      */
 } lbm_params;
 
 /* Diagnostics returned by lbm_reduce (FP64 accumulation).  "Light" weights a
@@ -277,7 +286,11 @@ lbm_status lbm_batch_set_config(lbm_batch_t *b, int choice);
 
 /* lbm_synchronize on every member: LBM_ERR_DIVERGED if any member produced a
  * non-finite phi or p*, LBM_ERR_CUDA if a TMA copy of a member's phi tile did
- * not complete (lbm_last_error on that member says which). */
+ * not complete (lbm_last_error on that member says which).  A block whose copy
+ * did not complete within the bounded wait returns while the copy may still
+ * land in shared memory that a later block of the same launch uses, so after
+ * that error the state of every member of the batch and the results of that
+ * launch are undefined: destroy the batch and create it again. */
 lbm_status lbm_batch_synchronize(lbm_batch_t *b);
 
 /* Text of the last failure of a batch call on b. */
@@ -298,7 +311,10 @@ void lbm_batch_destroy(lbm_batch_t *b);
  * Scratch space is a fixed array inside the library (about 786 KB per GPU, held
  * until the process exits): boxes of more than 134,217,728 cells (512^3) are
  * rejected with LBM_ERR_ARG.  The first call on a device looks up that array's
- * device address, so make that first call before any stream capture.  All calls
+ * device address, so make that first call before any stream capture.  The lookup
+ * is kept per device for the life of the process: it belongs to the device's
+ * primary context, so after cudaDeviceReset the kept address is stale and this
+ * entry point must not be called again in that process.  All calls
  * share the array and it keeps the last call's contents (each call overwrites
  * what it reads); calls that overlap on the GPU race on it, so the caller must
  * serialise them. */

@@ -101,12 +101,19 @@ lbm_status validate(const lbm_domain *d, const lbm_params *p, std::string &why) 
         return why = "phase_collision must be LBM_PHASE_SRT or LBM_PHASE_MRT", LBM_ERR_ARG;
     if (p->phase_collision == LBM_PHASE_MRT && p->precision != LBM_PRECISION_FP32)
         return why = "the MRT phase collision is built for FP32 storage", LBM_ERR_ARG;
-    if (p->kernel_form != LBM_FORM_FUSED && p->kernel_form != LBM_FORM_UNFUSED)
-        return why = "kernel_form must be LBM_FORM_FUSED or LBM_FORM_UNFUSED", LBM_ERR_ARG;
+    if (p->kernel_form != LBM_FORM_FUSED && p->kernel_form != LBM_FORM_UNFUSED &&
+        p->kernel_form != LBM_FORM_FUSED_CELL && p->kernel_form != LBM_FORM_FUSED_PAIR)
+        return why = "kernel_form must be LBM_FORM_FUSED, _UNFUSED, _FUSED_CELL or _FUSED_PAIR", LBM_ERR_ARG;
     if (p->kernel_form == LBM_FORM_UNFUSED && p->precision != LBM_PRECISION_FP32)
         return why = "the unfused form is built for FP32 storage", LBM_ERR_ARG;
+    if (p->kernel_form == LBM_FORM_FUSED_PAIR &&
+        (d->q_phase != 15 || p->phase_collision != LBM_PHASE_SRT || (d->q_hydro != 19 && d->q_hydro != 27) ||
+         d->nx % 2 != 0 || !lbm::offsets32((long long)d->nx * d->ny * d->nz, d->q_hydro, d->q_phase)))
+        return why = "the two-cell fused step needs nx even, q_phase 15 with SRT, q_hydro 19 or 27 and "
+                     "(q_hydro - 1) nx ny nz < 2^32",
+               LBM_ERR_ARG;
     if (d->q_phase != 15 && (p->precision != LBM_PRECISION_FP32 || p->phase_collision != LBM_PHASE_SRT ||
-                             p->kernel_form != LBM_FORM_FUSED))
+                             p->kernel_form == LBM_FORM_UNFUSED))
         return why = "the D2Q9 / D3Q19 / D3Q27 phase lattices run with FP32 storage, SRT, fused form", LBM_ERR_ARG;
     if (d->q_phase == 9 && p->gravity[2] != 0.0)
         return why = "the D2Q9 pair carries no z momentum: gravity[2] must be 0", LBM_ERR_ARG;
@@ -149,6 +156,7 @@ lbm::Params derive(const lbm_domain &d, const lbm_params &p) {
     k.phi_lo = p.clamp_phi ? 0.0f : -INFINITY;
     k.phi_hi = p.clamp_phi ? 1.0f : INFINITY;
     k.phase_mrt = p.phase_collision == LBM_PHASE_MRT ? 1 : 0;
+    k.step_form = p.kernel_form == LBM_FORM_FUSED_CELL || p.kernel_form == LBM_FORM_FUSED_PAIR ? p.kernel_form : 0;
     if (p.precision == LBM_PRECISION_FP32) {
         k.h_ref = 0.0f;
         k.g_scale = k.g_inv_scale = 1.0f;

@@ -127,6 +127,7 @@ struct Params {
     // h_i stored as h_i - w_i h_ref, g_i stored as g_i * g_scale
     float h_ref, g_scale, g_inv_scale;
     int phase_mrt;  // 1: MRT phase collision (selects the kernel instance on the host)
+    int step_form;  // fused step variant: 0 the library's choice, 2 one cell per thread, 3 two cells
 };
 
 // One lattice as seen by the auxiliary kernels: slot 0 (rest) in FP32, slot s >= 1

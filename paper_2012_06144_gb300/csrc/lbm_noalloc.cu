@@ -24,7 +24,8 @@
 // Host code may not use the array's name as a device address: in host code it
 // denotes a host-side stand-in.  The device address is obtained once per device
 // with cudaGetSymbolAddress, with that device current, on the first call that
-// runs on it, and kept for later calls.
+// runs on it, and kept for later calls (valid for the device's primary context:
+// a cudaDeviceReset makes it stale, as the public header states).
 #include <mutex>
 
 #include "lbm_internal.h"

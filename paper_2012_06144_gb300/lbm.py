@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR
                 -5: "LBM_ERR_STATE"}
 LBM_PRECISION_FP32, LBM_PRECISION_FP16, LBM_PRECISION_BF16 = 0, 1, 2
 LBM_PHASE_SRT, LBM_PHASE_MRT = 0, 1
-LBM_FORM_FUSED, LBM_FORM_UNFUSED = 0, 1
+LBM_FORM_FUSED, LBM_FORM_UNFUSED, LBM_FORM_FUSED_CELL, LBM_FORM_FUSED_PAIR = 0, 1, 2, 3
+FORMS = {"fused": LBM_FORM_FUSED, "unfused": LBM_FORM_UNFUSED, "cell": LBM_FORM_FUSED_CELL, "pair": LBM_FORM_FUSED_PAIR}
 PRECISIONS = {"fp32": LBM_PRECISION_FP32, "fp16": LBM_PRECISION_FP16, "bf16": LBM_PRECISION_BF16}
 DIAG_NAMES = ["mass", "mom_x", "mom_y", "mom_z", "light_vol", "light_x", "light_y", "light_z", "light_ux",
               "light_uy", "light_uz", "max_u"]
@@ -163,9 +164,11 @@ def make_params(rho_H=1.0, rho_ratio=1000.0, nu_H=0.01, mu_ratio=100.0, sigma=1e
     return p
 
 
-def from_problem(prob, precision=None):
+def from_problem(prob, precision=None, form=None):
     """(lbm_domain, lbm_params) of a ``workloads.Problem``-like object; ``precision``
-    ("fp32", "fp16", "bf16" or an LBM_PRECISION_* value) overrides the problem's."""
+    ("fp32", "fp16", "bf16" or an LBM_PRECISION_* value) overrides the problem's,
+    ``form`` ("fused", "unfused", "cell", "pair" or an LBM_FORM_* value) its kernel
+    form."""
     d = make_domain(prob.nx, prob.ny, prob.nz, prob.wall, prob.q_hydro, getattr(prob, "q_phase", 15))
     prec = getattr(prob, "precision", "fp32") if precision is None else precision
     prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
@@ -174,6 +177,8 @@ def from_problem(prob, precision=None):
                     store_phi_ref=float(getattr(prob, "store_phi_ref", 0.0)),
                     phase_collision=LBM_PHASE_MRT if getattr(prob, "phase_mrt", 0) else LBM_PHASE_SRT,
                     kernel_form=LBM_FORM_UNFUSED if getattr(prob, "unfused", 0) else LBM_FORM_FUSED)
+    if form is not None:
+        p.kernel_form = FORMS[form] if isinstance(form, str) else int(form)
     return d, p
 
 
@@ -339,8 +344,8 @@ class Simulation:
         self.N = domain.nx * domain.ny * domain.nz
 
     @classmethod
-    def from_problem(cls, prob, precision=None, **kw):
-        d, p = from_problem(prob, precision)
+    def from_problem(cls, prob, precision=None, form=None, **kw):
+        d, p = from_problem(prob, precision, form)
         return cls(d, p, **kw)
 
     def close(self):

@@ -95,7 +95,7 @@ def test_invalid_domain_rejected(lbm, field, value):
     ("rho_H", 0.0), ("rho_ratio", -1.0), ("nu_H", 0.0), ("mu_ratio", 0.0), ("sigma", -1e-4), ("xi", 0.0),
     ("mobility", 0.0), ("rho_ref", float("nan")), ("precision", 7), ("nu_H", float("inf")),
     ("store_g_scale", 3.0), ("store_g_scale", -4.0), ("store_phi_ref", float("inf")), ("clamp_phi", 2),
-    ("phase_collision", 2), ("phase_collision", -1), ("kernel_form", 2),
+    ("phase_collision", 2), ("phase_collision", -1), ("kernel_form", 4), ("kernel_form", -1),
 ])
 def test_invalid_params_rejected(lbm, field, value):
     p = lbm.make_params()
@@ -103,6 +103,25 @@ def test_invalid_params_rejected(lbm, field, value):
     with pytest.raises(lbm.LBMError) as ei:
         lbm.lbm_create(lbm.make_domain(8, 8, 8), p)
     assert ei.value.status == lbm.LBM_ERR_ARG
+
+
+@pytest.mark.parametrize("dom,prm", [
+    (dict(nx=7), {}),  # nx odd: a thread's two cells would straddle rows
+    (dict(q_phase=19), {}),
+    (dict(q_phase=27, q_hydro=27), {}),
+    ({}, dict(phase_collision=1)),
+])
+def test_pair_form_rejected_where_it_does_not_apply(lbm, dom, prm):
+    """The two-cell fused step needs nx even, the D3Q15 phase lattice with SRT and
+    D3Q19 / D3Q27 hydrodynamics: other problems are refused before any launch."""
+    args = dict(nx=8, ny=8, nz=8, q_hydro=27, q_phase=15)
+    args.update(dom)
+    d = lbm.make_domain(args["nx"], args["ny"], args["nz"], q_hydro=args["q_hydro"], q_phase=args["q_phase"])
+    p = lbm.make_params(kernel_form=lbm.LBM_FORM_FUSED_PAIR, **prm)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_create(d, p)
+    assert ei.value.status == lbm.LBM_ERR_ARG
+    assert "two-cell" in lbm.lbm_last_error(None)
 
 
 def test_too_many_cells_rejected(lbm):

@@ -41,10 +41,12 @@ def oracle_one_step(orc, prob, h, g, phi):
     return h_next, g_next, phi_next
 
 
-def test_static_droplet_200_steps(lbm, orc):
-    """32^3 periodic, D3Q15 + D3Q19, rho ratio 1000, 200 steps."""
+@pytest.mark.parametrize("form", ["fused", "cell"])
+def test_static_droplet_200_steps(lbm, orc, form):
+    """32^3 periodic, D3Q15 + D3Q19, rho ratio 1000, 200 steps; the default fused
+    step (two cells per thread on this even box) and the one-cell variant."""
     prob, phi0 = W.static_droplet()
-    sim = lbm.Simulation.from_problem(prob)
+    sim = lbm.Simulation.from_problem(prob, form=form)
     sim.init_phase(phi0)
     m0 = sim.reduce()["mass"]
     sim.step(200)

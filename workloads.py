@@ -21,7 +21,9 @@ Workloads (cell centres at i + 1/2, y is "up"):
   ``numpy.random.default_rng(6144)``; gravity with Eo = 10 at D = 24;
   buoyancy reference = mean density (periodic gravity axis).
 * ``precision_bubble`` 64^3 walled rising bubble, D = 16 at (32, 16, 32),
-  Eo = 10, Mo = 1e-3, t_ref = 1000.
+  Eo = 10, Mo = 1e-3, t_ref = 1000 (the storage formats' error case).
+* ``precision_timing`` 512^3 walled rising bubble, D = 32 at (256, 64, 256),
+  the rising-bubble parameters (the storage formats' timing case).
 * ``batched``          64 walled rising bubbles of four box sizes, seeded draws of
   density ratio and Eo (batched stepping).
 * ``roofline2d``       8192 x 16384 x 1 periodic, D2Q9 + D2Q9, light circles on a
@@ -226,6 +228,13 @@ def rising_bubble(nx: int = 128, ny: int = 512, nz: int = 128, D: float = 32.0, 
 
 def precision_bubble():
     return rising_bubble(64, 64, 64, D=16.0, centre=(32.0, 16.0, 32.0), t_ref=1000.0)
+
+
+def precision_timing(n: int = 512):
+    """The box the storage formats are timed on: the rising-bubble parameters
+    (D = 32, Eo 10, Mo 1e-3, t_ref 2000, density ratio 1000) on an n^3 box walled
+    on every face, the bubble at (n/2, 64, n/2)."""
+    return rising_bubble(n, n, n, D=32.0, centre=(n / 2, 64.0, n / 2), t_ref=2000.0)
 
 
 BATCH_SIZES = ((32, 32, 32), (48, 96, 48), (64, 128, 64), (96, 192, 96))
