@@ -10,7 +10,18 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
-    config.addinivalue_line("markers", "slow: longer CPU-only oracle runs")
+    config.addinivalue_line("markers", "slow: oracle runs of many minutes; run with LBM_RUN_SLOW=1")
+
+
+def pytest_collection_modifyitems(config, items):
+    """Tests marked slow (oracle runs of many minutes) are skipped unless
+    LBM_RUN_SLOW=1, so that the default CPU suite stays within a few minutes."""
+    if os.environ.get("LBM_RUN_SLOW") == "1":
+        return
+    skip = pytest.mark.skip(reason="slow oracle run: set LBM_RUN_SLOW=1")
+    for item in items:
+        if "slow" in item.keywords:
+            item.add_marker(skip)
 
 
 @pytest.fixture(scope="session")
