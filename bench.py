@@ -103,10 +103,12 @@ def apply_pair(args, prob, phi0, desc):
 
 def step_kernel_name(args, prob) -> str:
     """The kernel one step launches: the two-cells-per-thread fused step where it
-    applies and is chosen (every storage format by default: nx even, D3Q15 phase
-    lattice with D3Q19 / D3Q27 hydrodynamics), else the one-cell fused step."""
-    pair = (args.form in ("fused", "pair") and prob.nx % 2 == 0 and getattr(prob, "q_phase", 15) == 15
-            and prob.q_hydro in (19, 27))
+    applies and is chosen (every storage format by default: nx even, D3Q19 /
+    D3Q27 hydrodynamics with the D3Q15 phase lattice, or with D3Q19 / D3Q27 in
+    FP32), else the one-cell fused step."""
+    qp = getattr(prob, "q_phase", 15)
+    pair = (args.form in ("fused", "pair") and prob.nx % 2 == 0 and prob.q_hydro in (19, 27)
+            and (qp == 15 or (qp in (19, 27) and args.precision == "fp32")))
     name = "pair_step_kernel" if pair else "fused_step_kernel"
     return f"{name}<{args.precision}, hydro D3Q{prob.q_hydro}, phase D3Q{getattr(prob, 'q_phase', 15)}>"
 
@@ -379,10 +381,10 @@ def batched_form(args, stream, peak):
     bpc = bytes_per_cell(27, "fp32")
     out = {"members": len(batch), "cells": cells, "steps": steps, "value": cells / (ms / 1e3) / 1e6, "unit": UNIT,
            "ms_per_step": ms, "roofline_frac": cells * bpc / (ms / 1e3) / 1e9 / peak,
-           "tuned": {"tile": f"32x{shape[0]}x{shape[1]}", "order": order, "halo": halo,
+           "tuned": {"tile": lbm.batch_tile_name(shape), "order": order, "halo": halo,
                      "candidates_ms_per_step": {
-                         "{2}/32x{0[0]}x{0[1]}/{1}".format(*lbm.batch_candidate(i)): float(v)
-                         for i, v in enumerate(tune_ms)}},
+                         "{}/{}/{}".format(c[2], lbm.batch_tile_name(c[0]), c[1]): float(v)
+                         for i, v in enumerate(tune_ms) for c in [lbm.batch_candidate(i)]}},
            "per_member_launches": {"value": cells / (solo_ms / 1e3) / 1e6, "ms_per_step": solo_ms,
                                    "steps": solo_steps},
            "gpu_launches_per_step": (len(batch) + 63) // 64,

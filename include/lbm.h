@@ -222,7 +222,8 @@ void lbm_destroy(lbm_t *s);
  * Section 3 parameters; one hydrodynamic lattice for all) by the coupled step
  * of Algorithm 2, each exactly as lbm_step would advance it alone: one launch
  * per time step (per group of up to 64 members) runs one thread block per entry
- * of a table of the members' 32 x TY x TZ cell tiles.  Aimed at parameter
+ * of a table of the members' cell tiles (32 x TY x TZ cells with one cell per
+ * thread, or 32 x 4 x 2 with two).  Aimed at parameter
  * sweeps of small boxes, which alone cannot fill the GPU.
  *
  * Members are ordinary lbm_t handles owned by the batch (lbm_batch_member):
@@ -266,22 +267,25 @@ lbm_status lbm_batch_step(lbm_batch_t *b, int64_t n);
 /* Autotuner (the tile shapes and the halo staging of the batched step): for
  * each of 2 phi halo stagings (0: per-thread loads; 1: one TMA tensor copy per
  * block, walled faces mirrored in shared memory, per-thread loads for tiles on
- * a periodic face), 3 tile shapes (TY, TZ) = (4, 2), (8, 1), (2, 4) and 2 table
+ * a periodic face), 4 tile shapes (0, 1, 2: tiles of 32 x TY x TZ cells with one
+ * cell per thread, (TY, TZ) = (4, 2), (8, 1), (2, 4); 3: tiles of 32 x 4 x 2
+ * cells with two cells per thread, the LBM_FORM_FUSED_PAIR step) and 2 table
  * orders (0: member after member; 1: members' tiles dealt out round robin),
  * runs 1 + trial_steps batched steps, times the trial steps with CUDA events,
- * and keeps the fastest.  Candidate index: (halo * 3 + shape) * 2 + order.  The
+ * and keeps the fastest.  Candidate index: (halo * 4 + shape) * 2 + order.  The
  * trial steps are real time steps: every member advances by 1 + trial_steps per
  * timed candidate.  The TMA staging needs every member's nx to be a multiple of
- * 4 (and the CUDA driver's tensor-map support); otherwise its 6 candidates are
- * skipped and reported as -1.  choice (may be NULL) receives the winner's
- * index; ms_per_step (may be NULL) receives the 12 times by index.
- * Synchronises the stream. */
+ * 4 (and the CUDA driver's tensor-map support), shape 3 every member's nx even
+ * and per-thread loads; candidates that do not apply are skipped and reported
+ * as -1.  choice (may be NULL) receives the winner's index; ms_per_step (may be
+ * NULL) receives the 16 times by index.  Synchronises the stream. */
 lbm_status lbm_batch_tune(lbm_batch_t *b, int trial_steps, int *choice, double *ms_per_step);
 
 /* Selects candidate `choice` of lbm_batch_tune (same index) without timing.
- * LBM_ERR_ARG if choice is outside 0..11; LBM_ERR_STATE if it asks for the TMA
- * staging and these members do not allow it.  Host-only apart from uploading
- * the tile table (synchronises the stream). */
+ * LBM_ERR_ARG if choice is outside 0..15; LBM_ERR_STATE, with the configuration
+ * in use unchanged, if it asks for the TMA staging or the two-cell tiles and
+ * these members do not allow them.  Host-only apart from uploading the tile
+ * table (synchronises the stream). */
 lbm_status lbm_batch_set_config(lbm_batch_t *b, int choice);
 
 /* lbm_synchronize on every member: LBM_ERR_DIVERGED if any member produced a

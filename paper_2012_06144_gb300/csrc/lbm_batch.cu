@@ -30,7 +30,7 @@
 #include <cudaTypedefs.h>
 
 #include "lbm_handle.h"
-#include "lbm_step_impl.cuh"
+#include "lbm_pair_impl.cuh"
 
 namespace lbm {
 
@@ -59,11 +59,18 @@ struct GroupArgs {
 };
 static_assert(sizeof(GroupArgs) + 32 <= 32764, "kernel parameter block limit");
 
+// Tile shapes of the table: tx x ty x tz cells.  The first three run the one-cell
+// step (a thread per cell); the last the two-cell step of lbm_pair_impl.cuh (a
+// thread per pair of cells: 16 x 4 x 2 threads), for batches whose members all
+// have nx even, with per-thread halo loads.  All are 32 cells wide, the width
+// that keeps the tiles of the small walled boxes full.
 struct TileShape {
-    int ty, tz;
+    int ty, tz, tx;
 };
-constexpr TileShape kShapes[] = {{4, 2}, {8, 1}, {2, 4}};
-constexpr int kNumShapes = 3;
+constexpr int kPairTX = 16, kPairTY = 4, kPairTZ = 2;  // threads of the two-cell tile
+constexpr TileShape kShapes[] = {{4, 2, TX}, {8, 1, TX}, {2, 4, TX}, {kPairTY, kPairTZ, 2 * kPairTX}};
+constexpr int kNumShapes = 4;
+constexpr int kPairShape = 3;
 constexpr int kNumOrders = 2;  // 0: member after member, 1: members interleaved tile by tile
 constexpr int kNumHalos = 2;   // 0: per-thread loads, 1: TMA copy (per-thread loads on periodic faces)
 
@@ -125,6 +132,19 @@ __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
 }
 #endif
 
+// The two-cell step over the table: one block of 16 x 4 x 2 threads per entry
+// (member within the group, bx, by, bz) of 32 x 4 x 2 cells.
+template <int QG, bool G_SW, bool H_SW>
+__global__ void __launch_bounds__(kPairTX *kPairTY *kPairTZ, LBM_PAIR_MIN_BLOCKS)
+    batch_pair_kernel(const __grid_constant__ GroupArgs a, const int4 *__restrict__ tiles, int cur) {
+    __shared__ __align__(16) float tile[kPairTZ + 2][kPairTY + 2][2 * kPairTX + 4];
+    const int4 e = tiles[blockIdx.x];
+    const MemberDesc &d = a.m[e.x];
+    const pairstep::Lat<float> lh{d.h_rest, d.h_mov, (unsigned)d.p.N}, lg{d.g_rest, d.g_mov, (unsigned)d.p.N};
+    pairstep::pair_tile<float, QG, 15, G_SW, H_SW, kPairTX, kPairTY, kPairTZ, true>(
+        d.p, lh, lg, d.phi[cur], d.phi[cur ^ 1], d.flag, tile, e.y, e.z, e.w);
+}
+
 template <int QG, bool G_SW, bool H_SW, int TY, int TZ>
 static cudaError_t launch_shape(int halo, const GroupArgs &a, const int4 *tiles, int ntiles, int cur,
                                 cudaStream_t st) {
@@ -151,6 +171,10 @@ static cudaError_t launch_q(int shape, int halo, const GroupArgs &a, const int4 
         case 0: return launch_shape<QG, G_SW, H_SW, 4, 2>(halo, a, tiles, ntiles, cur, st);
         case 1: return launch_shape<QG, G_SW, H_SW, 8, 1>(halo, a, tiles, ntiles, cur, st);
         case 2: return launch_shape<QG, G_SW, H_SW, 2, 4>(halo, a, tiles, ntiles, cur, st);
+        case kPairShape:
+            if (halo) return cudaErrorInvalidValue;
+            batch_pair_kernel<QG, G_SW, H_SW><<<ntiles, dim3(kPairTX, kPairTY, kPairTZ), 0, st>>>(a, tiles, cur);
+            return cudaGetLastError();
         default: return cudaErrorInvalidValue;
     }
 }
@@ -211,6 +235,7 @@ struct lbm_batch_t {
     int shape = 0, order = 0, table_key = -1;
     int halo = 0;         // phi halo staging: 0 per-thread loads, 1 TMA copy
     bool tma_ok = false;  // every member's phi buffers have tensor maps
+    bool pair_ok = false; // every member has nx even: the two-cell tiles apply
     int map_shape = -1;   // the tile shape the tensor maps were encoded for
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // key: (t & 1) * 2 + cur
     std::string err;
@@ -238,7 +263,7 @@ struct TileGrid {
 
 TileGrid tile_grid(const lbm_domain &d, int shape) {
     const lbm::TileShape s = lbm::kShapes[shape];
-    return {(d.nx + lbm::TX - 1) / lbm::TX, (d.ny + s.ty - 1) / s.ty, (d.nz + s.tz - 1) / s.tz};
+    return {(d.nx + s.tx - 1) / s.tx, (d.ny + s.ty - 1) / s.ty, (d.nz + s.tz - 1) / s.tz};
 }
 
 void drop_graphs(lbm_batch_t *b) {
@@ -256,7 +281,7 @@ void drop_graphs(lbm_batch_t *b) {
 lbm_status build_table(lbm_batch_t *b, int shape, int order) {
     const int key = shape * lbm::kNumOrders + order;
     if (b->table_key == key) return LBM_OK;
-    if (b->tma_ok && b->map_shape != shape) {  // the TMA box is part of the tensor map
+    if (b->tma_ok && b->map_shape != shape && shape != lbm::kPairShape) {  // the TMA box is part of the tensor map
         const lbm::TileShape sh = lbm::kShapes[shape];
         for (size_t i = 0; i < b->m.size() && b->tma_ok; ++i) {
             CUtensorMap *maps = b->groups[i / lbm::kGroup].phi_map[i % lbm::kGroup];
@@ -451,6 +476,8 @@ lbm_status lbm_batch_create(lbm_batch_t **out, int count, const lbm_domain *doms
         d.flag = s->flag;
     }
     b->tma_ok = lbm::tensor_map_encoder() != nullptr;
+    b->pair_ok = true;
+    for (lbm_t *s : b->m) b->pair_ok = b->pair_ok && s->dom.nx % 2 == 0;
     const cudaError_t e = cudaMalloc(&b->d_tiles, (size_t)b->max_tiles * sizeof(int4));
     if (e != cudaSuccess) {
         lbm::set_thread_error(std::string("batch tile table: ") + cudaGetErrorString(e));
@@ -514,6 +541,10 @@ lbm_status lbm_batch_tune(lbm_batch_t *b, int trial_steps, int *choice, double *
         for (int sh = 0; sh < lbm::kNumShapes && st == LBM_OK; ++sh) {
             for (int od = 0; od < lbm::kNumOrders && st == LBM_OK; ++od) {
                 const int slot = (ha * lbm::kNumShapes + sh) * lbm::kNumOrders + od;
+                if (sh == lbm::kPairShape && (ha == 1 || !b->pair_ok)) {  // two-cell tiles: loads, nx even
+                    if (ms_per_step) ms_per_step[slot] = -1.0;
+                    continue;
+                }
                 st = build_table(b, sh, od);
                 if (st != LBM_OK) break;
                 if (ha == 1 && !b->tma_ok) {  // no tensor maps for these members
@@ -573,6 +604,8 @@ lbm_status lbm_batch_set_config(lbm_batch_t *b, int choice) {
     static const char *no_tma =
         "TMA halo staging unavailable (a member's nx is not a multiple of 4, or no driver support)";
     if (halo == 1 && !b->tma_ok) return b->err = no_tma, LBM_ERR_STATE;  // refused before anything changes
+    if (shape == lbm::kPairShape && (halo == 1 || !b->pair_ok))
+        return b->err = "the two-cell tiles need every member's nx even and per-thread halo loads", LBM_ERR_STATE;
     lbm_status st = build_table(b, shape, order);  // (re)encodes the tensor maps for the shape
     if (st != LBM_OK) return st;
     if (halo == 1 && !b->tma_ok) {

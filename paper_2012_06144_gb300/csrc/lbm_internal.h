@@ -42,8 +42,8 @@ inline bool offsets32(long long N, int q_hydro, int q_phase) {
 }
 
 // The two-cells-per-thread form of the fused step (lbm_pair.cu): taken where it
-// applies (nx even, the D3Q15 phase lattice with SRT, D3Q19 / D3Q27
-// hydrodynamics, 32-bit plane offsets) when the handle asks for it
+// applies (nx even, SRT, the D3Q15 phase lattice -- or D3Q19 / D3Q27 with FP32
+// storage -- with D3Q19 / D3Q27 hydrodynamics, 32-bit plane offsets) when the handle asks for it
 // (LBM_FORM_FUSED_PAIR) or, with LBM_FORM_FUSED, for the storage formats whose
 // bit (1 << precision) is set in LBM_PAIR.
 #ifndef LBM_PAIR
@@ -51,8 +51,8 @@ inline bool offsets32(long long N, int q_hydro, int q_phase) {
 #endif
 inline bool pair_step_enabled(int precision) { return ((LBM_PAIR >> precision) & 1) != 0; }
 bool pair_step_applies(const Params &p, int q_hydro, int q_phase, int precision);
-cudaError_t launch_pair_step(const Params &p, const Storage &sto, int q_hydro, bool g_swapped, bool h_swapped,
-                             const float *phi_in, float *phi_out, int *flag, cudaStream_t st);
+cudaError_t launch_pair_step(const Params &p, const Storage &sto, int q_hydro, int q_phase, bool g_swapped,
+                             bool h_swapped, const float *phi_in, float *phi_out, int *flag, cudaStream_t st);
 
 // One launch of the fused kernel K_k = hydro(k-1) + phase(k) (hydro = true), or
 // the first phase step alone (hydro = false).  g_swapped / h_swapped give the

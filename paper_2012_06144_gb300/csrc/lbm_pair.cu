@@ -1,656 +1,50 @@
-// lbm_pair.cu -- the fused coupled step with two cells per thread.
-//
-// The same update as fused_step_kernel (lbm_step.cu): one launch K_k advances
-// every cell by the hydrodynamic step k-1 and the phase-field step k of
-// Algorithm 2 (arXiv 2012.06144, Section 4.2), with the in-place AA streaming of
-// both lattices.  Here a thread owns the two neighbouring cells (x, x + 1),
-// x even, of one row, so that
-//   * the arithmetic of the two cells runs as packed FP32 pairs (one f32x2
-//     add, multiply or fused multiply-add of sm_100 and later per operation for
-//     both cells), halving the arithmetic instructions of the step;
-//   * a population whose two locations are neighbours in memory -- every
-//     population of the lattice in natural layout, and those of the swapped
-//     lattice that do not move along x -- is read and written as one 32-bit
-//     (16-bit storage) or 64-bit (FP32) access for both cells; the others (the
-//     swapped lattice's x-moving populations, whose locations x - e_x and
-//     x + 1 - e_x straddle two aligned pairs or wrap around the box) take one
-//     access per cell.
-// Needs nx even (so that every pair starts on an even element and a thread's
-// two cells are both inside or both outside the box) and the 32-bit plane
-// offsets of the single-cell kernel ((q - 1) N < 2^32); the D3Q15 phase lattice
-// with the SRT collision and D3Q19 or D3Q27 hydrodynamics.
-//
-// The arithmetic follows the single-cell kernel term by term (lbm_device.cuh,
-// lbm_step_impl.cuh) with the same reformulations: stencils from opposite-pair
-// differences grouped by weight class, moments from opposite-pair sums (D3Q27:
-// the x-y-z cascade), rest populations as exact remainders of the zeroth
-// moments, both lattices kept in their 16-bit storage units through the step.
-// Rounding differs from the single-cell kernel only where a multiply and an add
-// are fused differently.
-#include "lbm_step_impl.cuh"
+// lbm_pair.cu -- the fused coupled step with two cells per thread: the
+// single-simulation kernel and its launchers.  The device code, and what the
+// form does, are in lbm_pair_impl.cuh.
+#include "lbm_pair_impl.cuh"
 
-#ifndef LBM_PAIR_MIN_BLOCKS
-#define LBM_PAIR_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for (128 registers)
+#ifndef LBM_PAIR_MIN_BLOCKS_WIDE
+#define LBM_PAIR_MIN_BLOCKS_WIDE 3  // the same for pairs of lattices holding 46 or more populations
 #endif
 
 namespace lbm {
 namespace pairstep {
 
-constexpr int PX = 2 * TX;  // cells per block row: 32 threads x 2 cells
-#ifndef LBM_PAIR_TY
-#define LBM_PAIR_TY 2
-#endif
-#ifndef LBM_PAIR_TZ
-#define LBM_PAIR_TZ 2
-#endif
-constexpr int TY = LBM_PAIR_TY, TZ = LBM_PAIR_TZ;  // block tile: 64 x TY x TZ cells
-constexpr int ROW = PX + 4;  // phi tile row: columns 0..67 hold x0 - 2 .. x0 + 65
+template <int QG, int QP>
+constexpr int pair_min_blocks() { return QG + QP >= 46 ? LBM_PAIR_MIN_BLOCKS_WIDE : LBM_PAIR_MIN_BLOCKS; }
 
-// ---- packed FP32 arithmetic on (cell x, cell x + 1)
-__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
-__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 mul(float2 a, float s) { return __fmul2_rn(a, bc(s)); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 fma2(float2 a, float s, float2 c) { return __ffma2_rn(a, bc(s), c); }
-// a - b, exactly rounded: fma(b, -1, a)
-__device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, bc(-1.0f), a); }
-// acc + d or acc - d for a direction component of sign s (compile time)
-__device__ __forceinline__ float2 acc_signed(float2 acc, float2 d, int s) { return s > 0 ? add(acc, d) : sub(acc, d); }
-
-// ---- storage pairs: two consecutive elements of a plane
-template <typename T>
-struct PairOf;
-template <>
-struct PairOf<float> {
-    using P = float2;
-};
-template <>
-struct PairOf<__half> {
-    using P = __half2;
-};
-template <>
-struct PairOf<__nv_bfloat16> {
-    using P = __nv_bfloat162;
-};
-
-template <typename T>
-__device__ __forceinline__ float2 unpack(typename PairOf<T>::P v) {
-    if constexpr (std::is_same<T, __half>::value) return __half22float2(v);
-    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __bfloat1622float2(v);
-    else return v;
-}
-
-template <typename T>
-__device__ __forceinline__ typename PairOf<T>::P pack(float2 v) {
-    if constexpr (std::is_same<T, __half>::value) return __float22half2_rn(v);
-    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __float22bfloat162_rn(v);
-    else return v;
-}
-
-template <typename T>
-__device__ __forceinline__ T lo(typename PairOf<T>::P v) {
-    if constexpr (std::is_same<T, __half>::value) return __low2half(v);
-    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __low2bfloat16(v);
-    else return v.x;
-}
-
-template <typename T>
-__device__ __forceinline__ T hi(typename PairOf<T>::P v) {
-    if constexpr (std::is_same<T, __half>::value) return __high2half(v);
-    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __high2bfloat16(v);
-    else return v.y;
-}
-
-template <typename T>
-__device__ __forceinline__ typename PairOf<T>::P join(T a, T b) {
-    if constexpr (std::is_same<T, __half>::value) return __halves2half2(a, b);
-    else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __halves2bfloat162(a, b);
-    else return make_float2(a, b);
-}
-
-// One lattice: FP32 rest plane and q - 1 moving planes of type T, 32-bit element
-// offsets (s - 1) N + idx.
-template <typename T>
-struct Lat {
-    float *rest;
-    T *mov;
-    unsigned N;
-    __device__ __forceinline__ T *at(int s, int idx) const { return mov + ((unsigned)(s - 1) * N + (unsigned)idx); }
-};
-
-// Per-thread offsets of the pair: X[k] is the element index of x - 1 + k in the
-// cells' row (k = 0..3; periodic wrap, or clamp at a walled face), Y / Z the
-// offsets of the neighbouring rows / planes (0 at the centre); lo / hi the walled
-// faces touched by cell A = x (bits of lo[0], hi[0]) and cell B = x + 1.
-struct Nb4 {
-    int X[4], Y[3], Z[3];
-    int lo[2], hi[2];
-};
-
-__device__ __forceinline__ int nidx(const Nb4 &n, int k, int dx, int dy, int dz) {
-    return n.X[1 + k + dx] + n.Y[dy + 1] + n.Z[dz + 1];
-}
-
-// True if cell k's x + sign e leaves the box through a wall (EDGE: any walls in
-// the tile).
-template <int EDGE>
-__device__ __forceinline__ bool leaves(const Nb4 &n, int k, V3 e, int sign) {
-    if constexpr (EDGE == 0) return false;
-    const int ex = e.x * sign, ey = e.y * sign, ez = e.z * sign;
-    return (ex > 0 && (n.hi[k] & 1)) || (ex < 0 && (n.lo[k] & 1)) || (ey > 0 && (n.hi[k] & 2)) ||
-           (ey < 0 && (n.lo[k] & 2)) || (ez > 0 && (n.hi[k] & 4)) || (ez < 0 && (n.lo[k] & 4));
-}
-
-// (slot, element) of the pre-collision f_i of cell k (AA layout, lbm_device.cuh)
-template <int Q, bool SW, int EDGE>
-__device__ __forceinline__ void src(const Nb4 &n, int k, int i, int &slot, int &idx) {
-    const V3 e = vel<Q>(i);
-    if (!SW || leaves<EDGE>(n, k, e, -1)) {
-        slot = i;
-        idx = n.X[1 + k];
-        return;
-    }
-    slot = opp(i);
-    idx = nidx(n, k, -e.x, -e.y, -e.z);
-}
-
-// (slot, element) receiving the post-collision f*_i of cell k
-template <int Q, bool SW, int EDGE>
-__device__ __forceinline__ void dst(const Nb4 &n, int k, int i, int &slot, int &idx) {
-    const V3 e = vel<Q>(i);
-    if (!SW || leaves<EDGE>(n, k, e, +1)) {
-        slot = opp(i);
-        idx = n.X[1 + k];
-        return;
-    }
-    slot = i;
-    idx = nidx(n, k, e.x, e.y, e.z);
-}
-
-// True if both cells' locations of population i form one aligned pair: always in
-// natural layout; in swapped layout when e_x = 0 (y and z bounce-back is the
-// same for both cells of a row).
-template <int Q, bool SW>
-__device__ __forceinline__ constexpr bool paired(int i) {
-    return !SW || vel<Q>(i).x == 0;
-}
-
-// Pre-collision moving population f_i (i > 0) of both cells as stored (a
-// packed pair of the storage type; converted where it is used, so that the
-// loaded state occupies one register per population pair in 16-bit storage).
-template <typename T, int Q, bool SW, int EDGE>
-__device__ __forceinline__ typename PairOf<T>::P load_pop(const Lat<T> &L, const Nb4 &n, int i) {
-    using P = typename PairOf<T>::P;
-    if (paired<Q, SW>(i)) {
-        int slot, idx;
-        src<Q, SW, EDGE>(n, 0, i, slot, idx);
-        return ld_pop(reinterpret_cast<const P *>(L.at(slot, idx)));
-    }
-    int sa, ia, sb, ib;
-    src<Q, SW, EDGE>(n, 0, i, sa, ia);
-    src<Q, SW, EDGE>(n, 1, i, sb, ib);
-    return join<T>(ld_pop(L.at(sa, ia)), ld_pop(L.at(sb, ib)));
-}
-
-// the rest population of both cells (FP32, always at the cells themselves)
-__device__ __forceinline__ float2 load_rest(const float *rest, const Nb4 &n) {
-    return ld_pop(reinterpret_cast<const float2 *>(rest + n.X[1]));
-}
-
-// Stores the encoded post-collision f*_i of both cells.
-template <typename T, int Q, bool SW, int EDGE>
-__device__ __forceinline__ void store_pop(const Lat<T> &L, const Nb4 &n, int i, typename PairOf<T>::P v) {
-    using P = typename PairOf<T>::P;
-    if (paired<Q, SW>(i)) {
-        int slot, idx;
-        dst<Q, SW, EDGE>(n, 0, i, slot, idx);
-        *reinterpret_cast<P *>(L.at(slot, idx)) = v;
-        return;
-    }
-    int sa, ia, sb, ib;
-    dst<Q, SW, EDGE>(n, 0, i, sa, ia);
-    dst<Q, SW, EDGE>(n, 1, i, sb, ib);
-    st_pop(L.at(sa, ia), lo<T>(v));
-    st_pop(L.at(sb, ib), hi<T>(v));
-}
-
-// the rest population (always at the cells themselves)
-__device__ __forceinline__ void store_rest(float *rest, const Nb4 &n, float2 v) {
-    *reinterpret_cast<float2 *>(rest + n.X[1]) = v;
-}
-
-// Class sums of eq:grad / eq:lap for both cells (see stencil_sums), read from the
-// phi tile row by row: each row of the 3 x 3 neighbourhood is met together with
-// its opposite row, so only two rows are live at a time.
-struct Stencil2 {
-    float2 D1[3], D2[3], D3[3];
-    float2 L1, L2, L3;
-};
-
-struct Row3 {
-    float2 L, M, R;  // (x - 1, x), (x, x + 1), (x + 1, x + 2) of the row
-    __device__ __forceinline__ float2 at(int ex) const { return ex < 0 ? L : (ex > 0 ? R : M); }
-};
-
-// a tile row from the thread's columns: (x - 2, x - 1), (x, x + 1), (x + 2, x + 3)
-__device__ __forceinline__ Row3 tile_row(const float *row) {
-    const float2 a = *reinterpret_cast<const float2 *>(row), m = *reinterpret_cast<const float2 *>(row + 2),
-                 r = *reinterpret_cast<const float2 *>(row + 4);
-    return Row3{make_float2(a.y, m.x), m, make_float2(m.y, r.x)};
-}
-
-// the opposite pair (e, -e) with phi(x + e) = vp, phi(x - e) = vm into the class sums
-__device__ __forceinline__ void stencil_pair(Stencil2 &S, float2 vp, float2 vm, float2 c, int ex, int ey, int ez) {
-    const float2 D = sub(vp, vm), L = add(sub(vp, c), sub(vm, c));
-    const int cls = ex * ex + ey * ey + ez * ez;
-    float2 *Dc = cls == 1 ? S.D1 : (cls == 2 ? S.D2 : S.D3);
-    if (ex) Dc[0] = acc_signed(Dc[0], D, ex);
-    if (ey) Dc[1] = acc_signed(Dc[1], D, ey);
-    if (ez) Dc[2] = acc_signed(Dc[2], D, ez);
-    if (cls == 1) S.L1 = add(S.L1, L);
-    else if (cls == 2) S.L2 = add(S.L2, L);
-    else S.L3 = add(S.L3, L);
-}
-
-// rows(dy, dz): pointer to the tile row at offset (dy, dz) from the cells' row at
-// the thread's columns; centre receives phi of both cells
-template <typename RowPtr>
-__device__ __forceinline__ Stencil2 stencil_from_tile(const RowPtr &rows, float2 &centre) {
-    Stencil2 S;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) S.D1[a] = S.D2[a] = S.D3[a] = bc(0.f);
-    S.L1 = S.L2 = S.L3 = bc(0.f);
-    const Row3 r0 = tile_row(rows(0, 0));
-    const float2 c = r0.M;
-    centre = c;
-    stencil_pair(S, r0.R, r0.L, c, 1, 0, 0);
-    constexpr int DY[4] = {1, 0, 1, 1}, DZ[4] = {0, 1, 1, -1};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const Row3 rp = tile_row(rows(DY[k], DZ[k])), rm = tile_row(rows(-DY[k], -DZ[k]));
-#pragma unroll
-        for (int ex = -1; ex <= 1; ++ex) stencil_pair(S, rp.at(ex), rm.at(-ex), c, ex, DY[k], DZ[k]);
-    }
-    return S;
-}
-
-template <int Q>
-__device__ __forceinline__ void grad2(const Stencil2 &S, float2 &gx, float2 &gy, float2 &gz) {
-    constexpr float w1 = 3.f * wclass<Q>(1), w2 = 3.f * wclass<Q>(2), w3 = 3.f * wclass<Q>(3);
-    float2 g[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        g[a] = mul(S.D1[a], w1);
-        if (w2 != 0.f) g[a] = fma2(S.D2[a], w2, g[a]);
-        if (w3 != 0.f) g[a] = fma2(S.D3[a], w3, g[a]);
-    }
-    gx = g[0];
-    gy = g[1];
-    gz = g[2];
-}
-
-template <int Q>
-__device__ __forceinline__ float2 lap2(const Stencil2 &S) {
-    constexpr float w1 = 6.f * wclass<Q>(1), w2 = 6.f * wclass<Q>(2), w3 = 6.f * wclass<Q>(3);
-    float2 l = mul(S.L1, w1);
-    if (w2 != 0.f) l = fma2(S.L2, w2, l);
-    if (w3 != 0.f) l = fma2(S.L3, w3, l);
-    return l;
-}
-
-// moments of g (storage units) up to second order: p*, j, the second moments
-struct Moments2 {
-    float2 ps, jx, jy, jz, mxx, myy, mzz, mxy, mxz, myz;
-};
-
-template <int QG, typename G>
-__device__ __forceinline__ Moments2 moments2(const G &gv) {
-    Moments2 M;
-    if constexpr (QG == 27) {
-        // the x-y-z cascade of hydro_macro
-        float2 X0[3][3], X1[3][3], X2[3][3];
-#pragma unroll
-        for (int z = 0; z < 3; ++z)
-#pragma unroll
-            for (int y = 0; y < 3; ++y) {
-                const float2 a = gv(idx27(-1, y - 1, z - 1)), b = gv(idx27(0, y - 1, z - 1)),
-                             c = gv(idx27(1, y - 1, z - 1));
-                X2[z][y] = add(a, c);
-                X0[z][y] = add(X2[z][y], b);
-                X1[z][y] = sub(c, a);
-            }
-        float2 Y00[3], Y01[3], Y02[3], Y10[3], Y11[3], Y20[3];
-#pragma unroll
-        for (int z = 0; z < 3; ++z) {
-            Y02[z] = add(X0[z][0], X0[z][2]);
-            Y00[z] = add(Y02[z], X0[z][1]);
-            Y01[z] = sub(X0[z][2], X0[z][0]);
-            Y10[z] = add(add(X1[z][0], X1[z][2]), X1[z][1]);
-            Y11[z] = sub(X1[z][2], X1[z][0]);
-            Y20[z] = add(add(X2[z][0], X2[z][2]), X2[z][1]);
-        }
-        M.mzz = add(Y00[0], Y00[2]);
-        M.ps = add(M.mzz, Y00[1]);
-        M.jz = sub(Y00[2], Y00[0]);
-        M.jy = add(add(Y01[0], Y01[2]), Y01[1]);
-        M.myz = sub(Y01[2], Y01[0]);
-        M.myy = add(add(Y02[0], Y02[2]), Y02[1]);
-        M.jx = add(add(Y10[0], Y10[2]), Y10[1]);
-        M.mxz = sub(Y10[2], Y10[0]);
-        M.mxy = add(add(Y11[0], Y11[2]), Y11[1]);
-        M.mxx = add(add(Y20[0], Y20[2]), Y20[1]);
-    } else {
-        M.ps = gv(0);
-        M.jx = M.jy = M.jz = M.mxx = M.myy = M.mzz = M.mxy = M.mxz = M.myz = bc(0.f);
-#pragma unroll
-        for (int i = 1; i < QG; i += 2) {
-            const V3 e = vel<QG>(i);
-            const float2 s = add(gv(i), gv(i + 1)), d = sub(gv(i), gv(i + 1));
-            M.ps = add(M.ps, s);
-            if (e.x) { M.jx = acc_signed(M.jx, d, e.x); M.mxx = add(M.mxx, s); }
-            if (e.y) { M.jy = acc_signed(M.jy, d, e.y); M.myy = add(M.myy, s); }
-            if (e.z) { M.jz = acc_signed(M.jz, d, e.z); M.mzz = add(M.mzz, s); }
-            if (e.x && e.y) M.mxy = acc_signed(M.mxy, s, e.x * e.y);
-            if (e.x && e.z) M.mxz = acc_signed(M.mxz, s, e.x * e.z);
-            if (e.y && e.z) M.myz = acc_signed(M.myz, s, e.y * e.z);
-        }
-    }
-    return M;
-}
-
-// per-cell reciprocal (correctly rounded, as in the single-cell kernel)
-__device__ __forceinline__ float2 rcp2(float2 v) { return make_float2(__frcp_rn(v.x), __frcp_rn(v.y)); }
-__device__ __forceinline__ float2 clamp2(float2 v, float a, float b) {
-    return make_float2(fminf(fmaxf(v.x, a), b), fminf(fmaxf(v.y, a), b));
-}
-__device__ __forceinline__ bool finite_pair(float2 v) { return fabsf(v.x) < 1e30f && fabsf(v.y) < 1e30f; }
-
-// The collision of both lattices at the pair and the streaming stores, from the
-// pre-collision populations gv (g^{k-1}, storage units), hv (h^k, storage units)
-// and the neighbourhood nb of phi^{k-1}.  See collide_and_store.
-template <typename T, int QG, bool G_SW, bool H_SW, int EDGE>
-__device__ __forceinline__ void collide2(const Params &p, const Lat<T> &lh, const Lat<T> &lg, const Nb4 &n,
-                                         float2 grest, const typename PairOf<T>::P *gq, float2 hrest,
-                                         const typename PairOf<T>::P *hq, const Stencil2 &S, float2 phic,
-                                         float *__restrict__ phi_out, int *__restrict__ flag) {
-    using P = typename PairOf<T>::P;
-    constexpr bool F32 = std::is_same<T, float>::value;
-
-    // ---- hydrodynamic step k-1 (Section 3.2); g in storage units (the FP32 rest
-    // population times the scale)
-    const float2 g0 = F32 ? grest : mul(grest, p.g_scale);
-    auto gv = [&](int i) { return i == 0 ? g0 : unpack<T>(gq[i]); };
-    Moments2 M = moments2<QG>(gv);
-    if constexpr (!F32) {  // storage units -> values (a power of two: exact)
-        const float r = p.g_inv_scale;
-        M.ps = mul(M.ps, r);
-        M.jx = mul(M.jx, r);
-        M.jy = mul(M.jy, r);
-        M.jz = mul(M.jz, r);
-        M.mxx = mul(M.mxx, r);
-        M.myy = mul(M.myy, r);
-        M.mzz = mul(M.mzz, r);
-        M.mxy = mul(M.mxy, r);
-        M.mxz = mul(M.mxz, r);
-        M.myz = mul(M.myz, r);
-    }
-    float2 gpx, gpy, gpz;
-    grad2<QG>(S, gpx, gpy, gpz);
-    const float2 lap = lap2<QG>(S);
-    const float2 phim = clamp2(phic, p.phi_lo, p.phi_hi);
-    const float2 rho = fma2(phim, p.drho, bc(p.rho_L));  // eq:density
-    const float2 hir = mul(rcp2(rho), 0.5f);
-    const float2 tau = fma2(phim, p.dtau, bc(p.tau_L));
-    const float2 s_nu = rcp2(add(tau, bc(0.5f)));
-    const float2 grx = mul(gpx, p.drho), gry = mul(gpy, p.drho), grz = mul(gpz, p.drho);
-    // eq:chemPot, eq:surfaceTension: mu = 4 beta phi (phi - 1)(phi - 1/2) - kappa lap
-    const float2 cub = mul(mul(mul(phic, p.beta4), sub(phic, bc(1.0f))), sub(phic, bc(0.5f)));
-    const float2 mu = fma2(lap, -p.kappa, cub);
-    // eq:pressure_force, buoyancy
-    const float2 cp = mul(M.ps, -1.0f / 3.0f);
-    const float2 db = sub(rho, bc(p.rho_ref));
-    const float2 f0x = fma2(db, p.gx, fma2(cp, grx, mul(mu, gpx)));
-    const float2 f0y = fma2(db, p.gy, fma2(cp, gry, mul(mu, gpy)));
-    const float2 f0z = fma2(db, p.gz, fma2(cp, grz, mul(mu, gpz)));
-    // non-equilibrium second moments with u' (all forces but F_mu)
-    const float2 upx = fma2(f0x, hir, M.jx), upy = fma2(f0y, hir, M.jy), upz = fma2(f0z, hir, M.jz);
-    const float2 c3 = mul(M.ps, 1.0f / 3.0f);
-    const float2 a2xx = sub(M.mxx, c3), a2yy = sub(M.myy, c3), a2zz = sub(M.mzz, c3);
-    const float2 nupx = mul(upx, -1.0f), nupy = mul(upy, -1.0f), nupz = mul(upz, -1.0f);
-    const float2 pxx = fma2(upx, nupx, a2xx), pyy = fma2(upy, nupy, a2yy), pzz = fma2(upz, nupz, a2zz);
-    const float2 pxy = fma2(upx, nupy, M.mxy), pxz = fma2(upx, nupz, M.mxz), pyz = fma2(upy, nupz, M.myz);
-    // eq:viscousForce: F_mu = -tau s_nu Pi_neq . grad rho
-    const float2 cm = mul(mul(tau, s_nu), -1.0f);
-    const float2 Fx = fma2(cm, fma2(pxz, grz, fma2(pxy, gry, mul(pxx, grx))), f0x);
-    const float2 Fy = fma2(cm, fma2(pyz, grz, fma2(pyy, gry, mul(pxy, grx))), f0y);
-    const float2 Fz = fma2(cm, fma2(pzz, grz, fma2(pyz, gry, mul(pxz, grx))), f0z);
-    const float2 ux = fma2(Fx, hir, M.jx), uy = fma2(Fy, hir, M.jy), uz = fma2(Fz, hir, M.jz);
-
-    // eq:improved_collision in Hermite form (hydro_post), coefficients scaled to
-    // storage units
-    {
-        const float s = F32 ? 1.0f : p.g_scale;
-        const float2 r = sub(bc(1.0f), s_nu);
-        const float2 m0 = mul(M.ps, s);
-        const float2 m1x = mul(fma2(Fx, hir, ux), 3.0f * s), m1y = mul(fma2(Fy, hir, uy), 3.0f * s),
-                     m1z = mul(fma2(Fz, hir, uz), 3.0f * s);
-        const float2 bxx = fma2(mul(s_nu, ux), ux, mul(r, a2xx));
-        const float2 byy = fma2(mul(s_nu, uy), uy, mul(r, a2yy));
-        const float2 bzz = fma2(mul(s_nu, uz), uz, mul(r, a2zz));
-        const float2 Bxx = mul(bxx, 4.5f * s), Byy = mul(byy, 4.5f * s), Bzz = mul(bzz, 4.5f * s);
-        const float2 Bxy = mul(fma2(mul(s_nu, ux), uy, mul(r, M.mxy)), 9.0f * s);
-        const float2 Bxz = mul(fma2(mul(s_nu, ux), uz, mul(r, M.mxz)), 9.0f * s);
-        const float2 Byz = mul(fma2(mul(s_nu, uy), uz, mul(r, M.myz)), 9.0f * s);
-        const float2 m0t = sub(m0, mul(add(add(bxx, byy), bzz), 1.5f * s));
-        // the rest population takes p* - sum_{i>0} g*_i over the stored values
-        float2 gsum = bc(0.f);
-#pragma unroll
-        for (int i = 1; i < QG; i += 2) {
-            const V3 e = vel<QG>(i);
-            float2 ev = m0t, od = bc(0.f);
-            if (e.x) { od = acc_signed(od, m1x, e.x); ev = add(ev, Bxx); }
-            if (e.y) { od = acc_signed(od, m1y, e.y); ev = add(ev, Byy); }
-            if (e.z) { od = acc_signed(od, m1z, e.z); ev = add(ev, Bzz); }
-            if (e.x && e.y) ev = acc_signed(ev, Bxy, e.x * e.y);
-            if (e.x && e.z) ev = acc_signed(ev, Bxz, e.x * e.z);
-            if (e.y && e.z) ev = acc_signed(ev, Byz, e.y * e.z);
-            const float w = wgt<QG>(i);
-            const float2 E = mul(ev, w), O = mul(od, w);
-            const P qa = pack<T>(add(E, O)), qb = pack<T>(sub(E, O));
-            store_pop<T, QG, G_SW, EDGE>(lg, n, i, qa);
-            store_pop<T, QG, G_SW, EDGE>(lg, n, i + 1, qb);
-            gsum = add(gsum, add(unpack<T>(qa), unpack<T>(qb)));
-        }
-        if constexpr (!F32) gsum = mul(gsum, p.g_inv_scale);
-        store_rest(lg.rest, n, sub(M.ps, gsum));
-    }
-    if (!finite_pair(M.ps)) *flag = 1;
-
-    // ---- phase-field step k (Section 3.1), h in storage units q_i = h_i - w_i phi_ref
-    constexpr int QP = 15;
-    const float href = F32 ? 0.0f : p.h_ref;
-    float2 hv[QP];
-    hv[0] = hrest;
-#pragma unroll
-    for (int i = 1; i < QP; ++i) hv[i] = unpack<T>(hq[i]);
-    float2 pr[8];
-    pr[0] = F32 ? hv[0] : add(hv[0], bc(href * (1.0f - wgt<QP>(0))));
-#pragma unroll
-    for (int j = 0; j < 7; ++j) pr[j + 1] = add(hv[2 * j + 1], hv[2 * j + 2]);
-    const float2 phik = add(add(add(pr[0], pr[1]), add(pr[2], pr[3])), add(add(pr[4], pr[5]), add(pr[6], pr[7])));
-    *reinterpret_cast<float2 *>(phi_out + n.X[1]) = phik;
-    if (!finite_pair(phik)) *flag = 1;
-
-    float2 Gx, Gy, Gz;
-    grad2<QP>(S, Gx, Gy, Gz);
-    const float2 G2 = fma2(Gz, Gz, fma2(Gy, Gy, mul(Gx, Gx)));
-    float2 inv = bc(0.f);
-    if (G2.x > 1e-24f) inv.x = rsqrtf(G2.x);
-    if (G2.y > 1e-24f) inv.y = rsqrtf(G2.y);
-    // one Newton step: inv (1.5 - 0.5 G2 inv^2)
-    inv = mul(inv, fma2(mul(G2, -0.5f), mul(inv, inv), bc(1.5f)));
-    const float2 nx = mul(Gx, inv), ny = mul(Gy, inv), nz = mul(Gz, inv);
-    const float2 pc = sub(phic, bc(0.5f));
-    const float2 theta = mul(fma2(mul(pc, -4.0f), pc, bc(1.0f)), p.inv_xi);
-    // -1.5 u.u
-    const float2 nuu = mul(fma2(uz, uz, fma2(uy, uy, mul(ux, ux))), -1.5f);
-    const float om = p.omega_phi, fc = 1.0f - 0.5f * om;
-    const float2 phin = F32 ? phik : sub(phik, bc(href));
-    const float2 fth = mul(theta, fc);
-    // per weight class c (faces, corners): phi_k w_c times 4.5, -1.5 u.u and 3 (the
-    // velocity terms of h^eq), and the forcing factor (1 - omega/2) theta w_c
-    constexpr float w1 = wgt<QP>(1), w3 = wgt<QP>(7);
-    const float2 pw1 = mul(phik, w1), pw3 = mul(phik, w3);
-    const float2 A1 = mul(pw1, 4.5f), A3 = mul(pw3, 4.5f), B1 = mul(pw1, nuu), B3 = mul(pw3, nuu);
-    const float2 T1 = mul(pw1, 3.0f), T3 = mul(pw3, 3.0f), Fw1 = mul(fth, w1), Fw3 = mul(fth, w3);
-    float2 dsum = bc(0.f);
-#pragma unroll
-    for (int i = 1; i < QP; i += 2) {
-        const V3 e = vel<QP>(i);
-        const float w = wgt<QP>(i);
-        const bool face = w == w1;
-        float2 eu = bc(0.f), en = bc(0.f);
-        if (e.x) { eu = acc_signed(eu, ux, e.x); en = acc_signed(en, nx, e.x); }
-        if (e.y) { eu = acc_signed(eu, uy, e.y); en = acc_signed(en, ny, e.y); }
-        if (e.z) { eu = acc_signed(eu, uz, e.z); en = acc_signed(en, nz, e.z); }
-        // velocity terms of h^eq: phi_k w (4.5 (e.u)^2 - 1.5 u.u) +- phi_k w 3 e.u
-        const float2 x_even = fma2(mul(eu, face ? A1 : A3), eu, face ? B1 : B3);
-        const float2 x_odd = mul(eu, face ? T1 : T3);
-        const float2 F = mul(en, face ? Fw1 : Fw3);
-        // minus the non-equilibrium, q_i - (phi_k - phi_ref) w_i - (velocity terms),
-        // then q*_i = q_i + F_i - omega (minus the non-equilibrium)
-        const float2 ma = sub(fma2(phin, -w, hv[i]), add(x_even, x_odd));
-        const float2 mb = sub(fma2(phin, -w, hv[i + 1]), sub(x_even, x_odd));
-        const float2 a = fma2(ma, -om, add(hv[i], F));
-        const float2 b = fma2(mb, -om, sub(hv[i + 1], F));
-        const P qa = pack<T>(a), qb = pack<T>(b);
-        store_pop<T, QP, H_SW, EDGE>(lh, n, i, qa);
-        store_pop<T, QP, H_SW, EDGE>(lh, n, i + 1, qb);
-        dsum = add(dsum, add(sub(unpack<T>(qa), hv[i]), sub(unpack<T>(qb), hv[i + 1])));
-    }
-    store_rest(lh.rest, n, sub(hv[0], dsum));
-}
-
-// One tile of 64 x TY x TZ cells (32 x TY x TZ threads).
-template <typename T, int QG, bool G_SW, bool H_SW, int EDGE>
-__device__ __forceinline__ void pair_cells(const Params &p, const Lat<T> &lh, const Lat<T> &lg, const Nb4 &n,
-                                           bool active, const float *__restrict__ phi_in,
-                                           float (*tile)[TY + 2][ROW], float *__restrict__ phi_out,
-                                           int *__restrict__ flag, int bx, int by, int bz, int tx, int ty, int tz) {
-    constexpr int HY = TY + 2, HZ = TZ + 2, NROW = HY * HZ, NWARP = TY * TZ, RPW = (NROW + NWARP - 1) / NWARP;
-    const int lane = tx, warp = ty + TY * tz;
-    const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
-    // phi^{k-1} rows of the tile with a one-cell halo: columns 1..66 = x0 - 1 .. x0 + 64
-    const int gx0 = min(wrap_or_clamp(bx * PX - 1 + lane, p.nx, wx), p.nx - 1);
-    const int gx1 = min(wrap_or_clamp(bx * PX + 31 + lane, p.nx, wx), p.nx - 1);
-    const int gx2 = min(wrap_or_clamp(bx * PX + 63 + lane, p.nx, wx), p.nx - 1);
-    float tv0[RPW], tv1[RPW], tv2[RPW];
-#pragma unroll
-    for (int k = 0; k < RPW; ++k) {
-        const int r = warp + k * NWARP;
-        if (r < NROW) {
-            const int kz = r / HY, ky = r - kz * HY;
-            const int gy = min(wrap_or_clamp(by * TY - 1 + ky, p.ny, wy), p.ny - 1);
-            const int gz = min(wrap_or_clamp(bz * TZ - 1 + kz, p.nz, wz), p.nz - 1);
-            const float *row = phi_in + (size_t)gy * p.nx + (size_t)gz * p.nx * p.ny;
-            tv0[k] = __ldg(row + gx0);
-            tv1[k] = __ldg(row + gx1);
-            if (lane < 2) tv2[k] = __ldg(row + gx2);
-        }
-    }
-    constexpr int QP = 15;
-    using P = typename PairOf<T>::P;
-    P gq[QG], hq[QP];
-    float2 grest, hrest;
-    if (active) {
-        grest = load_rest(lg.rest, n);
-#pragma unroll
-        for (int i = 1; i < QG; ++i) gq[i] = load_pop<T, QG, G_SW, EDGE>(lg, n, i);
-        hrest = load_rest(lh.rest, n);
-#pragma unroll
-        for (int i = 1; i < QP; ++i) hq[i] = load_pop<T, QP, H_SW, EDGE>(lh, n, i);
-    }
-#pragma unroll
-    for (int k = 0; k < RPW; ++k) {
-        const int r = warp + k * NWARP;
-        if (r < NROW) {
-            const int kz = r / HY, ky = r - kz * HY;
-            tile[kz][ky][1 + lane] = tv0[k];
-            tile[kz][ky][33 + lane] = tv1[k];
-            if (lane < 2) tile[kz][ky][65 + lane] = tv2[k];
-        }
-    }
-    __syncthreads();
-    if (!active) return;
-    float2 phic;
-    const Stencil2 S = stencil_from_tile(
-        [&](int dy, int dz) { return &tile[tz + 1 + dz][ty + 1 + dy][2 * lane]; }, phic);
-    collide2<T, QG, G_SW, H_SW, EDGE>(p, lh, lg, n, grest, gq, hrest, hq, S, phic, phi_out, flag);
-}
-
-template <typename T, int QG, bool G_SW, bool H_SW>
-__global__ void __launch_bounds__(TX *TY *TZ, LBM_PAIR_MIN_BLOCKS)
+template <typename T, int QG, int QP, bool G_SW, bool H_SW>
+__global__ void __launch_bounds__(TX *TY *TZ, pair_min_blocks<QG, QP>())
     pair_step_kernel(Params p, Lat<T> lh, Lat<T> lg, const float *__restrict__ phi_in, float *__restrict__ phi_out,
                      int *__restrict__ flag) {
     __shared__ __align__(16) float tile[TZ + 2][TY + 2][ROW];
+    // blockIdx.x runs over the (x, y) tiles, x fastest; blockIdx.y over z
     const int nbx = (p.nx + PX - 1) / PX;
-    const int by = blockIdx.x / nbx, bx = blockIdx.x - by * nbx, bz = blockIdx.y;
-    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-    const int x = bx * PX + 2 * tx, y = by * TY + ty, z = bz * TZ + tz;
-    const bool active = x < p.nx && y < p.ny && z < p.nz;  // nx even: x + 1 < nx as well
-
-    const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
-    const int xc = min(x, p.nx - 2), yc = min(y, p.ny - 1), zc = min(z, p.nz - 1);
-    const int nxy = p.nx * p.ny;
-    const int c = xc + p.nx * yc + nxy * zc;
-    Nb4 n;
-    n.X[0] = c + wrap_or_clamp(xc - 1, p.nx, wx) - xc;
-    n.X[1] = c;
-    n.X[2] = c + 1;
-    n.X[3] = c + wrap_or_clamp(xc + 2, p.nx, wx) - xc;
-    n.Y[0] = (wrap_or_clamp(yc - 1, p.ny, wy) - yc) * p.nx;
-    n.Y[1] = 0;
-    n.Y[2] = (wrap_or_clamp(yc + 1, p.ny, wy) - yc) * p.nx;
-    n.Z[0] = (wrap_or_clamp(zc - 1, p.nz, wz) - zc) * nxy;
-    n.Z[1] = 0;
-    n.Z[2] = (wrap_or_clamp(zc + 1, p.nz, wz) - zc) * nxy;
-    const int lyz = (wy && yc == 0 ? 2 : 0) | (wz && zc == 0 ? 4 : 0);
-    const int hyz = (wy && yc == p.ny - 1 ? 2 : 0) | (wz && zc == p.nz - 1 ? 4 : 0);
-    n.lo[0] = lyz | (wx && xc == 0 ? 1 : 0);
-    n.hi[0] = hyz;
-    n.lo[1] = lyz;
-    n.hi[1] = hyz | (wx && xc + 1 == p.nx - 1 ? 1 : 0);
-
-    const bool ex = wx && (bx == 0 || (bx + 1) * PX >= p.nx), ey = wy && (by == 0 || (by + 1) * TY >= p.ny),
-               ez = wz && (bz == 0 || (bz + 1) * TZ >= p.nz);
-    if (!(ex || ey || ez))
-        pair_cells<T, QG, G_SW, H_SW, 0>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx, by, bz, tx, ty, tz);
-    else
-        pair_cells<T, QG, G_SW, H_SW, 7>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx, by, bz, tx, ty, tz);
+    const int by = blockIdx.x / nbx, bx = blockIdx.x - by * nbx;
+    pair_tile<T, QG, QP, G_SW, H_SW>(p, lh, lg, phi_in, phi_out, flag, tile, bx, by, blockIdx.y);
 }
 
-template <typename T, int QG, bool G_SW, bool H_SW>
+template <typename T, int QG, int QP, bool G_SW, bool H_SW>
 cudaError_t launch_pair(const Params &p, const Storage &sto, const float *pi, float *po, int *flag,
                         cudaStream_t st) {
     const Lat<T> lh{sto.h.rest, static_cast<T *>(sto.h.mov), (unsigned)p.N};
     const Lat<T> lg{sto.g.rest, static_cast<T *>(sto.g.mov), (unsigned)p.N};
     const dim3 block(TX, TY, TZ);
     const dim3 grid(((p.nx + PX - 1) / PX) * ((p.ny + TY - 1) / TY), (p.nz + TZ - 1) / TZ);
-    pair_step_kernel<T, QG, G_SW, H_SW><<<grid, block, 0, st>>>(p, lh, lg, pi, po, flag);
+    pair_step_kernel<T, QG, QP, G_SW, H_SW><<<grid, block, 0, st>>>(p, lh, lg, pi, po, flag);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int QP>
 cudaError_t launch_pair_layouts(const Params &p, const Storage &sto, int q_hydro, bool g_sw, bool h_sw,
                                 const float *pi, float *po, int *flag, cudaStream_t st) {
     if (g_sw == h_sw) return cudaErrorInvalidValue;
     if (q_hydro == 27)
-        return g_sw ? launch_pair<T, 27, true, false>(p, sto, pi, po, flag, st)
-                    : launch_pair<T, 27, false, true>(p, sto, pi, po, flag, st);
+        return g_sw ? launch_pair<T, 27, QP, true, false>(p, sto, pi, po, flag, st)
+                    : launch_pair<T, 27, QP, false, true>(p, sto, pi, po, flag, st);
     if (q_hydro == 19)
-        return g_sw ? launch_pair<T, 19, true, false>(p, sto, pi, po, flag, st)
-                    : launch_pair<T, 19, false, true>(p, sto, pi, po, flag, st);
+        return g_sw ? launch_pair<T, 19, QP, true, false>(p, sto, pi, po, flag, st)
+                    : launch_pair<T, 19, QP, false, true>(p, sto, pi, po, flag, st);
     return cudaErrorInvalidValue;
 }
 
@@ -659,20 +53,30 @@ cudaError_t launch_pair_layouts(const Params &p, const Storage &sto, int q_hydro
 bool pair_step_applies(const Params &p, int q_hydro, int q_phase, int precision) {
     if (p.step_form == LBM_FORM_FUSED_CELL) return false;
     if (p.step_form != LBM_FORM_FUSED_PAIR && !pair_step_enabled(precision)) return false;
-    return q_phase == 15 && !p.phase_mrt && (q_hydro == 19 || q_hydro == 27) && (p.nx % 2) == 0 &&
+    // the D3Q19 / D3Q27 phase lattices are stored in FP32 (checked on creation)
+    const bool qp_ok = q_phase == 15 || ((q_phase == 19 || q_phase == 27) && precision == LBM_PRECISION_FP32);
+    return qp_ok && !p.phase_mrt && (q_hydro == 19 || q_hydro == 27) && (p.nx % 2) == 0 &&
            offsets32(p.N, q_hydro, q_phase);
 }
 
-cudaError_t launch_pair_step(const Params &p, const Storage &sto, int q_hydro, bool g_sw, bool h_sw,
+cudaError_t launch_pair_step(const Params &p, const Storage &sto, int q_hydro, int q_phase, bool g_sw, bool h_sw,
                              const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
+    if (q_phase != 15) {
+        if (sto.precision != LBM_PRECISION_FP32) return cudaErrorInvalidValue;
+        if (q_phase == 19)
+            return pairstep::launch_pair_layouts<float, 19>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
+        if (q_phase == 27)
+            return pairstep::launch_pair_layouts<float, 27>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
+        return cudaErrorInvalidValue;
+    }
     switch (sto.precision) {
         case LBM_PRECISION_FP32:
-            return pairstep::launch_pair_layouts<float>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
+            return pairstep::launch_pair_layouts<float, 15>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
         case LBM_PRECISION_FP16:
-            return pairstep::launch_pair_layouts<__half>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
+            return pairstep::launch_pair_layouts<__half, 15>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
         case LBM_PRECISION_BF16:
-            return pairstep::launch_pair_layouts<__nv_bfloat16>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag,
-                                                                st);
+            return pairstep::launch_pair_layouts<__nv_bfloat16, 15>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out,
+                                                                    flag, st);
         default:
             return cudaErrorInvalidValue;
     }

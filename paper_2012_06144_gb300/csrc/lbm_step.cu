@@ -154,7 +154,7 @@ static Planes planes_of(const Params &p, const Storage &sto, int q_hydro, int q_
 cudaError_t launch_step(const Params &p, const Storage &sto, int q_hydro, int q_phase, bool g_sw, bool h_sw,
                         bool hydro, const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
     if (hydro && pair_step_applies(p, q_hydro, q_phase, sto.precision))
-        return launch_pair_step(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
+        return launch_pair_step(p, sto, q_hydro, q_phase, g_sw, h_sw, phi_in, phi_out, flag, st);
     // the MRT phase collision and the D3Q19 / D3Q27 phase lattices: FP32 storage
     if (p.phase_mrt || q_phase != 15) {
         if (sto.precision != LBM_PRECISION_FP32) return cudaErrorInvalidValue;

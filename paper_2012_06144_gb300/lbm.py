@@ -84,15 +84,22 @@ _SIGNATURES = {
     "lbm_batch_last_error": ([_VP], ctypes.c_char_p),
     "lbm_batch_destroy": ([_VP], None),
 }
-BATCH_SHAPES = [(4, 2), (8, 1), (2, 4)]  # (TY, TZ) of the autotuner's tile shapes, in its order
+BATCH_SHAPES = [(4, 2), (8, 1), (2, 4), "pair"]  # the autotuner's tile shapes, in its order: (TY, TZ) of
+# 32 x TY x TZ cells with one cell per thread, and "pair", 32 x 4 x 2 cells with two cells per thread
 BATCH_ORDERS = ["member", "round_robin"]
 BATCH_HALOS = ["loads", "tma"]  # phi halo staging: per-thread loads, or one TMA tensor copy per block
 
 
 def batch_choice(shape, order, halo="loads") -> int:
     """Candidate index of lbm_batch_tune / lbm_batch_set_config."""
-    return (BATCH_HALOS.index(halo) * len(BATCH_SHAPES) + BATCH_SHAPES.index(tuple(shape))) * len(BATCH_ORDERS) + \
+    shape = shape if isinstance(shape, str) else tuple(shape)
+    return (BATCH_HALOS.index(halo) * len(BATCH_SHAPES) + BATCH_SHAPES.index(shape)) * len(BATCH_ORDERS) + \
         BATCH_ORDERS.index(order)
+
+
+def batch_tile_name(shape) -> str:
+    """Cells of a tile shape, e.g. "32x4x2", and "32x4x2/pair" for the two-cell tile."""
+    return "32x4x2/pair" if shape == "pair" else f"32x{shape[0]}x{shape[1]}"
 
 
 def batch_candidate(choice: int):

@@ -107,13 +107,12 @@ def test_invalid_params_rejected(lbm, field, value):
 
 @pytest.mark.parametrize("dom,prm", [
     (dict(nx=7), {}),  # nx odd: a thread's two cells would straddle rows
-    (dict(q_phase=19), {}),
-    (dict(q_phase=27, q_hydro=27), {}),
+    (dict(nz=1, q_phase=9, q_hydro=9), {}),
     ({}, dict(phase_collision=1)),
 ])
 def test_pair_form_rejected_where_it_does_not_apply(lbm, dom, prm):
-    """The two-cell fused step needs nx even, the D3Q15 phase lattice with SRT and
-    D3Q19 / D3Q27 hydrodynamics: other problems are refused before any launch."""
+    """The two-cell fused step needs nx even, the SRT phase collision and the
+    three-dimensional lattices: other problems are refused before any launch."""
     args = dict(nx=8, ny=8, nz=8, q_hydro=27, q_phase=15)
     args.update(dom)
     d = lbm.make_domain(args["nx"], args["ny"], args["nz"], q_hydro=args["q_hydro"], q_phase=args["q_phase"])
@@ -307,14 +306,14 @@ def test_pattern_probe_is_built_and_checks_its_arguments(lbm):
 
 def test_batch_candidate_index_round_trip(lbm):
     """The binding's candidate index matches the C tuner's layout
-    (halo * 3 + shape) * 2 + order, over all 12 candidates, and the C entry point
-    refuses indices outside 0..11 without touching CUDA."""
+    (halo * 4 + shape) * 2 + order, over all 16 candidates, and the C entry point
+    refuses indices outside 0..15 without touching CUDA."""
     seen = set()
     for i in range(len(lbm.BATCH_HALOS) * len(lbm.BATCH_SHAPES) * len(lbm.BATCH_ORDERS)):
         shape, order, halo = lbm.batch_candidate(i)
         assert lbm.batch_choice(shape, order, halo) == i
-        assert i == (lbm.BATCH_HALOS.index(halo) * 3 + lbm.BATCH_SHAPES.index(shape)) * 2 + lbm.BATCH_ORDERS.index(order)
+        assert i == (lbm.BATCH_HALOS.index(halo) * 4 + lbm.BATCH_SHAPES.index(shape)) * 2 + lbm.BATCH_ORDERS.index(order)
         seen.add((shape, order, halo))
-    assert len(seen) == 12
+    assert len(seen) == 16 and lbm.batch_tile_name("pair") == "32x4x2/pair"
     lib = lbm.load()
     assert lib.lbm_batch_set_config(None, 0) == lbm.LBM_ERR_ARG

@@ -133,16 +133,17 @@ def test_members_match_single_runs(lbm, orc, stream, q):
 
 
 def test_tuner_visits_every_candidate(lbm, orc, stream):
-    """The tuner's trial steps are real steps through all 3 tile shapes x 2 table
-    orders; these members (nx not a multiple of 4) have no TMA staging, so its 6
-    candidates are skipped.  The members must still match single runs afterwards."""
+    """The tuner's trial steps are real steps through the one-cell tile shapes x
+    2 table orders; these members (some nx odd) have neither the two-cell tiles
+    nor the TMA staging, so those 10 candidates are skipped.  The members must still match single runs afterwards."""
     members = _members(27)
     batch = lbm.Batch.from_problems([p for p, _ in members], stream=stream)
     for m, (_, phi0) in zip(batch.members, members):
         m.init_phase(phi0)
     shape, order, halo, ms = batch.tune(trial_steps=2)
     assert shape in lbm.BATCH_SHAPES and order in lbm.BATCH_ORDERS and halo == "loads"
-    assert ms.shape == (12,) and np.all(ms[:6] > 0) and np.all(ms[6:] == -1.0)
+    # odd nx: no two-cell tiles (candidates 6, 7) and no TMA staging (8..15)
+    assert ms.shape == (16,) and np.all(ms[:6] > 0) and np.all(ms[6:] == -1.0)
     assert batch.steps_done() == 6 * 3
     with pytest.raises(lbm.LBMError) as e:
         batch.configure((4, 2), "member", "tma")
@@ -239,19 +240,61 @@ def test_tma_halo_staging(lbm, orc, stream, q, shape):
 
 
 def test_tuner_with_tma_candidates(lbm, orc, stream):
-    """With TMA-capable members the tuner times all 12 candidates."""
+    """With TMA-capable members (nx multiples of 4) the tuner times 14 candidates:
+    every one but the two-cell tiles with TMA staging."""
     members = _tma_members(27)
     batch = lbm.Batch.from_problems([p for p, _ in members], stream=stream)
     for m, (_, phi0) in zip(batch.members, members):
         m.init_phase(phi0)
     shape, order, halo, ms = batch.tune(trial_steps=2)
-    assert ms.shape == (12,) and np.all(ms > 0)
+    assert ms.shape == (16,) and np.all(ms[:14] > 0) and np.all(ms[14:] == -1.0)
     assert halo in lbm.BATCH_HALOS
-    assert batch.steps_done() == 12 * 3
+    assert batch.steps_done() == 14 * 3
     batch.step(5)
     batch.synchronize()
     for m, (prob, phi0) in zip(batch.members, members):
-        _assert_as_close_as_single(orc, lbm, m, prob, phi0, 12 * 3 + 5)
+        _assert_as_close_as_single(orc, lbm, m, prob, phi0, 14 * 3 + 5)
+    batch.close()
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_two_cell_tiles(lbm, orc, stream, q):
+    """The two-cells-per-thread tiles (32 x 4 x 2 cells) on members with nx even,
+    walled and periodic faces and ragged tails: two steps from a random state
+    against the FP64 oracle population by population, then plain and
+    graph-replayed steps as close to the oracle as single runs; a batch with an
+    odd nx refuses the shape."""
+    members = _tma_members(q)
+    states = [W.random_state(p, seed=51 + k) for k, (p, _) in enumerate(members)]
+    batch = lbm.Batch.from_problems([p for p, _ in members], stream=stream)
+    batch.configure("pair", "round_robin", "loads")
+    for m, st in zip(batch.members, states):
+        m.set_state(*st)
+    batch.step(2)
+    batch.synchronize()
+    for m, (prob, _), (h, g, phi) in zip(batch.members, members, states):
+        op = orc.make_problem(prob)
+        for _ in range(2):
+            g, u = orc.hydro_step(op, g.astype(np.float64), phi.astype(np.float64))
+            h, phi = orc.phase_step(op, h.astype(np.float64), phi.astype(np.float64), u)
+        for a, b in zip(m.get_state(), (h, g, phi)):
+            assert np.abs(a - b).max() <= TOL * np.abs(b).max()
+    batch.close()
+    batch = lbm.Batch.from_problems([p for p, _ in members], stream=stream)
+    batch.configure("pair", "member", "loads")
+    for m, (_, phi0) in zip(batch.members, members):
+        m.init_phase(phi0)
+    batch.step(3)
+    batch.step(16)
+    batch.synchronize()
+    for m, (prob, phi0) in zip(batch.members, members):
+        _assert_as_close_as_single(orc, lbm, m, prob, phi0, 19)
+    batch.close()
+    odd = _members(q)
+    batch = lbm.Batch.from_problems([p for p, _ in odd], stream=stream)
+    with pytest.raises(lbm.LBMError) as e:
+        batch.configure("pair", "member", "loads")
+    assert e.value.status == lbm.LBM_ERR_STATE
     batch.close()
 
 

@@ -31,7 +31,8 @@ def rel_linf(a, b, floor=0.0):
 
 
 @pytest.mark.parametrize("qp,q", PAIRS)
-@pytest.mark.parametrize("nx,ny,nz,wall", [(37, 29, 19, (0, 0, 0)), (33, 17, 11, (1, 1, 1))])
+@pytest.mark.parametrize("nx,ny,nz,wall", [(37, 29, 19, (0, 0, 0)), (33, 17, 11, (1, 1, 1)),
+                                           (38, 29, 19, (0, 0, 0)), (66, 17, 11, (1, 1, 1))])
 def test_two_steps_from_random_state(lbm, orc, qp, q, nx, ny, nz, wall):
     prob = W.Problem(nx, ny, nz, wall=wall, q_hydro=q, q_phase=qp, rho_ratio=100.0, mu_ratio=30.0, sigma=1e-3,
                      xi=3.0, mobility=0.03, gravity=(1e-5, -2e-5, 3e-6), rho_ref=0.4)
@@ -53,11 +54,13 @@ def test_two_steps_from_random_state(lbm, orc, qp, q, nx, ny, nz, wall):
         assert rel_linf(g1, rg) <= TOL, step
 
 
+@pytest.mark.parametrize("form", ["fused", "cell"])
 @pytest.mark.parametrize("qp,q", [(19, 19), (27, 27)])
-def test_static_droplet_200_steps(lbm, orc, qp, q):
+def test_static_droplet_200_steps(lbm, orc, qp, q, form):
+    """32^3 (nx even: the two-cell step by default) and the one-cell step."""
     prob, phi0 = W.static_droplet(q_hydro=q)
     prob.q_phase = qp
-    sim = lbm.Simulation.from_problem(prob)
+    sim = lbm.Simulation.from_problem(prob, form=form)
     sim.init_phase(phi0)
     sim.step(200)
     sim.synchronize()
