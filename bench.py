@@ -104,13 +104,15 @@ def apply_pair(args, prob, phi0, desc):
 def step_kernel_name(args, prob) -> str:
     """The kernel one step launches: the two-cells-per-thread fused step where it
     applies and is chosen (every storage format by default: nx even, D3Q19 /
-    D3Q27 hydrodynamics with the D3Q15 phase lattice, or with D3Q19 / D3Q27 in
-    FP32), else the one-cell fused step."""
+    D3Q27 hydrodynamics with the D3Q15 phase lattice, or in FP32 with the D3Q19
+    / D3Q27 phase lattices, and the D2Q9 pair), else the one-cell fused step."""
     qp = getattr(prob, "q_phase", 15)
-    pair = (args.form in ("fused", "pair") and prob.nx % 2 == 0 and prob.q_hydro in (19, 27)
-            and (qp == 15 or (qp in (19, 27) and args.precision == "fp32")))
+    lattices = ((qp == 15 and prob.q_hydro in (19, 27))
+                or (args.precision == "fp32" and ((qp in (19, 27) and prob.q_hydro in (19, 27)) or qp == 9)))
+    pair = args.form in ("fused", "pair") and prob.nx % 2 == 0 and lattices
     name = "pair_step_kernel" if pair else "fused_step_kernel"
-    return f"{name}<{args.precision}, hydro D3Q{prob.q_hydro}, phase D3Q{getattr(prob, 'q_phase', 15)}>"
+    d = "D2Q" if qp == 9 else "D3Q"
+    return f"{name}<{args.precision}, hydro {d}{prob.q_hydro}, phase {d}{qp}>"
 
 
 def measured_hbm_peak():

@@ -107,10 +107,10 @@ lbm_status validate(const lbm_domain *d, const lbm_params *p, std::string &why) 
     if (p->kernel_form == LBM_FORM_UNFUSED && p->precision != LBM_PRECISION_FP32)
         return why = "the unfused form is built for FP32 storage", LBM_ERR_ARG;
     if (p->kernel_form == LBM_FORM_FUSED_PAIR &&
-        (d->q_phase == 9 || p->phase_collision != LBM_PHASE_SRT || (d->q_hydro != 19 && d->q_hydro != 27) ||
-         d->nx % 2 != 0 || !lbm::offsets32((long long)d->nx * d->ny * d->nz, d->q_hydro, d->q_phase)))
-        return why = "the two-cell fused step needs nx even, the SRT phase collision, q_phase 15, 19 or 27, "
-                     "q_hydro 19 or 27 and (max(q) - 1) nx ny nz < 2^32",
+        (p->phase_collision != LBM_PHASE_SRT || d->nx % 2 != 0 ||
+         !lbm::offsets32((long long)d->nx * d->ny * d->nz, d->q_hydro, d->q_phase)))
+        return why = "the two-cell fused step needs nx even, the SRT phase collision and "
+                     "(max(q) - 1) nx ny nz < 2^32",
                LBM_ERR_ARG;
     if (d->q_phase != 15 && (p->precision != LBM_PRECISION_FP32 || p->phase_collision != LBM_PHASE_SRT ||
                              p->kernel_form == LBM_FORM_UNFUSED))

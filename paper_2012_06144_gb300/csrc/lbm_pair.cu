@@ -6,22 +6,38 @@
 #ifndef LBM_PAIR_MIN_BLOCKS_WIDE
 #define LBM_PAIR_MIN_BLOCKS_WIDE 3  // the same for pairs of lattices holding 46 or more populations
 #endif
+#ifndef LBM_PAIR_MIN_BLOCKS_2D
+#define LBM_PAIR_MIN_BLOCKS_2D 6  // and for the two-dimensional pair (8192 x 16384, MLUPS: 4 blocks 41,586, 5: 43,991, 6: 45,029, 7: 43,886)
+#endif
 
 namespace lbm {
 namespace pairstep {
 
 template <int QG, int QP>
-constexpr int pair_min_blocks() { return QG + QP >= 46 ? LBM_PAIR_MIN_BLOCKS_WIDE : LBM_PAIR_MIN_BLOCKS; }
+constexpr int pair_min_blocks() {
+    return QP == 9 ? LBM_PAIR_MIN_BLOCKS_2D : (QG + QP >= 46 ? LBM_PAIR_MIN_BLOCKS_WIDE : LBM_PAIR_MIN_BLOCKS);
+}
+
+#ifndef LBM_PAIR_TY2D
+#define LBM_PAIR_TY2D 4
+#endif
+
+// Tile of the step: 64 x 2 x 2 cells, or 64 x LBM_PAIR_TY2D x 1 for the two-dimensional pair
+template <int QP>
+constexpr int pair_ty() { return QP == 9 ? LBM_PAIR_TY2D : TY; }
+template <int QP>
+constexpr int pair_tz() { return QP == 9 ? 1 : TZ; }
 
 template <typename T, int QG, int QP, bool G_SW, bool H_SW>
-__global__ void __launch_bounds__(TX *TY *TZ, pair_min_blocks<QG, QP>())
+__global__ void __launch_bounds__(TX *pair_ty<QP>() * pair_tz<QP>(), pair_min_blocks<QG, QP>())
     pair_step_kernel(Params p, Lat<T> lh, Lat<T> lg, const float *__restrict__ phi_in, float *__restrict__ phi_out,
                      int *__restrict__ flag) {
-    __shared__ __align__(16) float tile[TZ + 2][TY + 2][ROW];
+    constexpr int TYk = pair_ty<QP>(), TZk = pair_tz<QP>();
+    __shared__ __align__(16) float tile[TZk + 2][TYk + 2][ROW];
     // blockIdx.x runs over the (x, y) tiles, x fastest; blockIdx.y over z
     const int nbx = (p.nx + PX - 1) / PX;
     const int by = blockIdx.x / nbx, bx = blockIdx.x - by * nbx;
-    pair_tile<T, QG, QP, G_SW, H_SW>(p, lh, lg, phi_in, phi_out, flag, tile, bx, by, blockIdx.y);
+    pair_tile<T, QG, QP, G_SW, H_SW, TX, TYk, TZk>(p, lh, lg, phi_in, phi_out, flag, tile, bx, by, blockIdx.y);
 }
 
 template <typename T, int QG, int QP, bool G_SW, bool H_SW>
@@ -29,8 +45,9 @@ cudaError_t launch_pair(const Params &p, const Storage &sto, const float *pi, fl
                         cudaStream_t st) {
     const Lat<T> lh{sto.h.rest, static_cast<T *>(sto.h.mov), (unsigned)p.N};
     const Lat<T> lg{sto.g.rest, static_cast<T *>(sto.g.mov), (unsigned)p.N};
-    const dim3 block(TX, TY, TZ);
-    const dim3 grid(((p.nx + PX - 1) / PX) * ((p.ny + TY - 1) / TY), (p.nz + TZ - 1) / TZ);
+    constexpr int TYk = pair_ty<QP>(), TZk = pair_tz<QP>();
+    const dim3 block(TX, TYk, TZk);
+    const dim3 grid(((p.nx + PX - 1) / PX) * ((p.ny + TYk - 1) / TYk), (p.nz + TZk - 1) / TZk);
     pair_step_kernel<T, QG, QP, G_SW, H_SW><<<grid, block, 0, st>>>(p, lh, lg, pi, po, flag);
     return cudaGetLastError();
 }
@@ -48,21 +65,34 @@ cudaError_t launch_pair_layouts(const Params &p, const Storage &sto, int q_hydro
     return cudaErrorInvalidValue;
 }
 
+// the two-dimensional pair: D2Q9 for both lattices
+template <typename T>
+cudaError_t launch_pair_2d(const Params &p, const Storage &sto, bool g_sw, bool h_sw, const float *pi, float *po,
+                           int *flag, cudaStream_t st) {
+    if (g_sw == h_sw) return cudaErrorInvalidValue;
+    return g_sw ? launch_pair<T, 9, 9, true, false>(p, sto, pi, po, flag, st)
+                : launch_pair<T, 9, 9, false, true>(p, sto, pi, po, flag, st);
+}
+
 }  // namespace pairstep
 
 bool pair_step_applies(const Params &p, int q_hydro, int q_phase, int precision) {
     if (p.step_form == LBM_FORM_FUSED_CELL) return false;
     if (p.step_form != LBM_FORM_FUSED_PAIR && !pair_step_enabled(precision)) return false;
-    // the D3Q19 / D3Q27 phase lattices are stored in FP32 (checked on creation)
-    const bool qp_ok = q_phase == 15 || ((q_phase == 19 || q_phase == 27) && precision == LBM_PRECISION_FP32);
-    return qp_ok && !p.phase_mrt && (q_hydro == 19 || q_hydro == 27) && (p.nx % 2) == 0 &&
-           offsets32(p.N, q_hydro, q_phase);
+    // the D3Q19 / D3Q27 phase lattices and the D2Q9 pair are stored in FP32
+    // (checked on creation)
+    const bool f32 = precision == LBM_PRECISION_FP32;
+    const bool lat_ok = (q_phase == 15 && (q_hydro == 19 || q_hydro == 27)) ||
+                        ((q_phase == 19 || q_phase == 27) && (q_hydro == 19 || q_hydro == 27) && f32) ||
+                        (q_phase == 9 && q_hydro == 9 && f32);
+    return lat_ok && !p.phase_mrt && (p.nx % 2) == 0 && offsets32(p.N, q_hydro, q_phase);
 }
 
 cudaError_t launch_pair_step(const Params &p, const Storage &sto, int q_hydro, int q_phase, bool g_sw, bool h_sw,
                              const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
     if (q_phase != 15) {
         if (sto.precision != LBM_PRECISION_FP32) return cudaErrorInvalidValue;
+        if (q_phase == 9) return pairstep::launch_pair_2d<float>(p, sto, g_sw, h_sw, phi_in, phi_out, flag, st);
         if (q_phase == 19)
             return pairstep::launch_pair_layouts<float, 19>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
         if (q_phase == 27)

@@ -260,7 +260,8 @@ __device__ __forceinline__ void stencil_pair(Stencil2 &S, float2 vp, float2 vm, 
 
 // rows(dy, dz): pointer to the tile row at offset (dy, dz) from the cells' row at
 // the thread's columns; centre receives phi of both cells
-template <typename RowPtr>
+// PLANE: the in-plane neighbours only (the D2Q9 pair on an nx x ny x 1 box).
+template <bool PLANE = false, typename RowPtr>
 __device__ __forceinline__ Stencil2 stencil_from_tile(const RowPtr &rows, float2 &centre) {
     Stencil2 S;
 #pragma unroll
@@ -272,7 +273,7 @@ __device__ __forceinline__ Stencil2 stencil_from_tile(const RowPtr &rows, float2
     stencil_pair(S, r0.R, r0.L, c, 1, 0, 0);
     constexpr int DY[4] = {1, 0, 1, 1}, DZ[4] = {0, 1, 1, -1};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < (PLANE ? 1 : 4); ++k) {
         const Row3 rp = tile_row(rows(DY[k], DZ[k])), rm = tile_row(rows(-DY[k], -DZ[k]));
 #pragma unroll
         for (int ex = -1; ex <= 1; ++ex) stencil_pair(S, rp.at(ex), rm.at(-ex), c, ex, DY[k], DZ[k]);
@@ -428,7 +429,8 @@ __device__ __forceinline__ void collide2(const Params &p, const Lat<T> &lh, cons
     // non-equilibrium second moments with u' (all forces but F_mu)
     const float2 upx = fma2(f0x, hir, M.jx), upy = fma2(f0y, hir, M.jy), upz = fma2(f0z, hir, M.jz);
     const float2 c3 = mul(M.ps, 1.0f / 3.0f);
-    const float2 a2xx = sub(M.mxx, c3), a2yy = sub(M.myy, c3), a2zz = sub(M.mzz, c3);
+    // Hermite second moments over the lattice's own dimensions (no zz for D2Q9)
+    const float2 a2xx = sub(M.mxx, c3), a2yy = sub(M.myy, c3), a2zz = QG == 9 ? bc(0.f) : sub(M.mzz, c3);
     const float2 nupx = mul(upx, -1.0f), nupy = mul(upy, -1.0f), nupz = mul(upz, -1.0f);
     const float2 pxx = fma2(upx, nupx, a2xx), pyy = fma2(upy, nupy, a2yy), pzz = fma2(upz, nupz, a2zz);
     const float2 pxy = fma2(upx, nupy, M.mxy), pxz = fma2(upx, nupz, M.mxz), pyz = fma2(upy, nupz, M.myz);
@@ -565,7 +567,9 @@ __device__ __forceinline__ void pair_cells(const Params &p, const Lat<T> &lh, co
                                            float (*tile)[TYT + 2][2 * TXT + 4], float *__restrict__ phi_out,
                                            int *__restrict__ flag, int bx, int by, int bz, int tx, int ty, int tz) {
     using Sh = PairShape<TXT, TYT, TZT>;
-    constexpr int HY = TYT + 2, HZ = TZT + 2, NROW = HY * HZ;
+    // the D2Q9 pair (nx x ny x 1 box): only the cells' own plane, kept as tile[1]
+    constexpr bool PLANE = QP == 9;
+    constexpr int HY = TYT + 2, HZ = TZT + 2, NROW = PLANE ? HY : HY * HZ;
     const bool wx = p.wall & 1, wy = p.wall & 2, wz = p.wall & 4;
     // phi^{k-1} rows of the tile with a one-cell halo (periodic wrap or wall
     // mirror per axis; coordinates past a ragged box end are clamped into the box,
@@ -574,10 +578,13 @@ __device__ __forceinline__ void pair_cells(const Params &p, const Lat<T> &lh, co
     constexpr int NWARP = Sh::NT / 32;
     constexpr int EPT = TXT == 32 ? (NROW + NWARP - 1) / NWARP * 3 : (NROW * W + Sh::NT - 1) / Sh::NT;
     float tv[EPT];
+    // row r of the tile: (kz, ky) = (r / HY, r % HY), or (1, r) in a plane
+    auto row_kz = [&](int r) { return PLANE ? 1 : r / HY; };
+    auto row_ky = [&](int r) { return PLANE ? r : r - (r / HY) * HY; };
     auto row_ptr = [&](int r) {
-        const int kz = r / HY, ky = r - kz * HY;
+        const int kz = row_kz(r), ky = row_ky(r);
         const int gy = min(wrap_or_clamp(by * TYT - 1 + ky, p.ny, wy), p.ny - 1);
-        const int gz = min(wrap_or_clamp(bz * TZT - 1 + kz, p.nz, wz), p.nz - 1);
+        const int gz = PLANE ? bz : min(wrap_or_clamp(bz * TZT - 1 + kz, p.nz, wz), p.nz - 1);
         return phi_in + (size_t)gy * p.nx + (size_t)gz * p.nx * p.ny;
     };
     auto gx = [&](int k) { return min(wrap_or_clamp(bx * Sh::PXT - 1 + k, p.nx, wx), p.nx - 1); };
@@ -621,7 +628,7 @@ __device__ __forceinline__ void pair_cells(const Params &p, const Lat<T> &lh, co
         for (int j = 0; j < EPT / 3; ++j) {
             const int r = warp + j * NWARP;
             if (r < NROW) {
-                const int kz = r / HY, ky = r - kz * HY;
+                const int kz = row_kz(r), ky = row_ky(r);
                 tile[kz][ky][1 + lane] = tv[3 * j];
                 tile[kz][ky][33 + lane] = tv[3 * j + 1];
                 if (lane < 2) tile[kz][ky][65 + lane] = tv[3 * j + 2];
@@ -633,16 +640,16 @@ __device__ __forceinline__ void pair_cells(const Params &p, const Lat<T> &lh, co
         for (int j = 0; j < EPT; ++j) {
             const int e = tid + j * Sh::NT;
             if (e < NROW * W) {
-                const int r = e / W, k = e - r * W, kz = r / HY, ky = r - kz * HY;
-                tile[kz][ky][1 + k] = tv[j];
+                const int r = e / W, k = e - r * W;
+                tile[row_kz(r)][row_ky(r)][1 + k] = tv[j];
             }
         }
     }
     __syncthreads();
     if (!active) return;
     float2 phic;
-    const Stencil2 S = stencil_from_tile(
-        [&](int dy, int dz) { return &tile[tz + 1 + dz][ty + 1 + dy][2 * tx]; }, phic);
+    const Stencil2 S = stencil_from_tile<PLANE>(
+        [&](int dy, int dz) { return &tile[PLANE ? 1 : tz + 1 + dz][ty + 1 + dy][2 * tx]; }, phic);
     collide2<T, QG, QP, G_SW, H_SW, EDGE>(p, lh, lg, n, grest, gq, hrest, hq, S, phic, phi_out, flag);
 }
 

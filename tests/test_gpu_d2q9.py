@@ -29,7 +29,8 @@ def rel_linf(a, b, floor=0.0):
     return float(np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), floor))
 
 
-@pytest.mark.parametrize("nx,ny,wall", [(37, 29, (0, 0, 0)), (33, 17, (1, 1, 0)), (70, 9, (0, 1, 0))])
+@pytest.mark.parametrize("nx,ny,wall", [(37, 29, (0, 0, 0)), (33, 17, (1, 1, 0)), (70, 9, (0, 1, 0)),
+                                        (38, 29, (0, 0, 0)), (130, 17, (1, 1, 0)), (2, 11, (1, 0, 0))])
 def test_two_steps_from_random_state(lbm, orc, nx, ny, wall):
     prob = W.Problem(nx, ny, 1, wall=wall, q_hydro=9, q_phase=9, rho_ratio=100.0, mu_ratio=30.0, sigma=1e-3,
                      xi=3.0, mobility=0.03, gravity=(1e-5, -2e-5, 0.0), rho_ref=0.4)
@@ -50,11 +51,12 @@ def test_two_steps_from_random_state(lbm, orc, nx, ny, wall):
         assert rel_linf(g1, rg) <= TOL, step
 
 
-def test_droplet_200_steps(lbm, orc):
+@pytest.mark.parametrize("form", ["fused", "cell"])
+def test_droplet_200_steps(lbm, orc, form):
     prob = W.Problem(48, 48, 1, q_hydro=9, q_phase=9, rho_ratio=1000.0, nu_H=0.01, mu_ratio=100.0, sigma=1e-4,
                      xi=5.0, mobility=0.02)
     phi0 = W.cylinder_phi(prob, (24.0, 24.0), 10.0, heavy_inside=True).astype(np.float32)
-    sim = lbm.Simulation.from_problem(prob)
+    sim = lbm.Simulation.from_problem(prob, form=form)
     sim.init_phase(phi0)
     sim.step(200)
     sim.synchronize()
