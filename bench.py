@@ -126,10 +126,12 @@ def measured_hbm_peak():
 
 
 def kernel_source_hash() -> str:
-    """Hash of the fused kernel's sources with comments and blank space removed
-    (a change of comments leaves the recorded counters valid)."""
+    """Hash of the fused step's sources (both fused kernels) with comments and
+    blank space removed (a change of comments leaves the recorded counters
+    valid)."""
     h = hashlib.sha256()
-    for f in ("lbm_step.cu", "lbm_pair.cu", "lbm_step_impl.cuh", "lbm_device.cuh", "lbm_internal.h"):
+    for f in ("lbm_step.cu", "lbm_pair.cu", "lbm_pair_impl.cuh", "lbm_step_impl.cuh", "lbm_device.cuh",
+              "lbm_internal.h"):
         with open(os.path.join(ROOT, "paper_2012_06144_gb300", "csrc", f)) as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
