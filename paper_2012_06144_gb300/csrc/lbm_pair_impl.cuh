@@ -36,6 +36,9 @@
 #ifndef LBM_PAIR_MIN_BLOCKS
 #define LBM_PAIR_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for (128 registers)
 #endif
+#ifndef LBM_PAIR_MIXED
+#define LBM_PAIR_MIXED 1  // 16-bit storage: sums of stored values by mixed-precision adds (0: convert, then add)
+#endif
 
 namespace lbm {
 namespace pairstep {
@@ -111,6 +114,40 @@ __device__ __forceinline__ typename PairOf<T>::P join(T a, T b) {
     if constexpr (std::is_same<T, __half>::value) return __halves2half2(a, b);
     else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __halves2bfloat162(a, b);
     else return make_float2(a, b);
+}
+
+// Mixed-precision add and subtract of sm_100 and later: the 16-bit operand is
+// widened inside the FP32 operation (cvt(a) + c, cvt(a) - c), which spares the
+// separate conversion -- on this GPU a conversion costs the multiply-add pipe
+// twice what an add does, and the 16-bit steps are held back by that pipe.
+template <typename T>
+__device__ __forceinline__ float madd(T a, float c) {
+    float d;
+    if constexpr (std::is_same<T, __half>::value)
+        asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(a)), "f"(c));
+    else
+        asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(a)), "f"(c));
+    return d;
+}
+
+template <typename T>
+__device__ __forceinline__ float msub(T a, float c) {
+    float d;
+    if constexpr (std::is_same<T, __half>::value)
+        asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(a)), "f"(c));
+    else
+        asm("sub.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(__bfloat16_as_ushort(a)), "f"(c));
+    return d;
+}
+
+// the same for both cells of a stored pair: cvt(q) + c, cvt(q) - c
+template <typename T>
+__device__ __forceinline__ float2 madd2(typename PairOf<T>::P q, float2 c) {
+    return make_float2(madd<T>(lo<T>(q), c.x), madd<T>(hi<T>(q), c.y));
+}
+template <typename T>
+__device__ __forceinline__ float2 msub2(typename PairOf<T>::P q, float2 c) {
+    return make_float2(msub<T>(lo<T>(q), c.x), msub<T>(hi<T>(q), c.y));
 }
 
 // One lattice: FP32 rest plane and q - 1 moving planes of type T, 32-bit element
@@ -372,6 +409,47 @@ __device__ __forceinline__ float2 tree_sum2(const float2 *a) {
     else return add(tree_sum2<LO, N / 2>(a), tree_sum2<LO + N / 2, N - N / 2>(a));
 }
 
+// The D3Q27 moments of 16-bit stored populations by the same x-y-z cascade, with
+// each line's first-level sums taken by mixed-precision operations: per line
+// (a, b, c) along x only a is converted; a + c, (a + c) + b and c - a widen c and
+// b inside the adds.  The same sums, in the same order, as moments2.
+template <typename T>
+__device__ __forceinline__ Moments2 moments27_mixed(const typename PairOf<T>::P *gq, float2 g0) {
+    float2 X0[3][3], X1[3][3], X2[3][3];
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+            const int ia = idx27(-1, y - 1, z - 1), ib = idx27(0, y - 1, z - 1), ic = idx27(1, y - 1, z - 1);
+            const float2 a = unpack<T>(gq[ia]);
+            X2[z][y] = madd2<T>(gq[ic], a);
+            X0[z][y] = ib == 0 ? add(X2[z][y], g0) : madd2<T>(gq[ib], X2[z][y]);
+            X1[z][y] = msub2<T>(gq[ic], a);
+        }
+    Moments2 M;
+    float2 Y00[3], Y01[3], Y02[3], Y10[3], Y11[3], Y20[3];
+#pragma unroll
+    for (int z = 0; z < 3; ++z) {
+        Y02[z] = add(X0[z][0], X0[z][2]);
+        Y00[z] = add(Y02[z], X0[z][1]);
+        Y01[z] = sub(X0[z][2], X0[z][0]);
+        Y10[z] = add(add(X1[z][0], X1[z][2]), X1[z][1]);
+        Y11[z] = sub(X1[z][2], X1[z][0]);
+        Y20[z] = add(add(X2[z][0], X2[z][2]), X2[z][1]);
+    }
+    M.mzz = add(Y00[0], Y00[2]);
+    M.ps = add(M.mzz, Y00[1]);
+    M.jz = sub(Y00[2], Y00[0]);
+    M.jy = add(add(Y01[0], Y01[2]), Y01[1]);
+    M.myz = sub(Y01[2], Y01[0]);
+    M.myy = add(add(Y02[0], Y02[2]), Y02[1]);
+    M.jx = add(add(Y10[0], Y10[2]), Y10[1]);
+    M.mxz = sub(Y10[2], Y10[0]);
+    M.mxy = add(add(Y11[0], Y11[2]), Y11[1]);
+    M.mxx = add(add(Y20[0], Y20[2]), Y20[1]);
+    return M;
+}
+
 // per-cell reciprocal (correctly rounded, as in the single-cell kernel)
 __device__ __forceinline__ float2 rcp2(float2 v) { return make_float2(__frcp_rn(v.x), __frcp_rn(v.y)); }
 __device__ __forceinline__ float2 clamp2(float2 v, float a, float b) {
@@ -394,7 +472,9 @@ __device__ __forceinline__ void collide2(const Params &p, const Lat<T> &lh, cons
     // population times the scale)
     const float2 g0 = F32 ? grest : mul(grest, p.g_scale);
     auto gv = [&](int i) { return i == 0 ? g0 : unpack<T>(gq[i]); };
-    Moments2 M = moments2<QG>(gv);
+    Moments2 M;
+    if constexpr (!F32 && QG == 27 && LBM_PAIR_MIXED) M = moments27_mixed<T>(gq, g0);
+    else M = moments2<QG>(gv);
     if constexpr (!F32) {  // storage units -> values (a power of two: exact)
         const float r = p.g_inv_scale;
         M.ps = mul(M.ps, r);
@@ -474,7 +554,8 @@ __device__ __forceinline__ void collide2(const Params &p, const Lat<T> &lh, cons
             const P qa = pack<T>(add(E, O)), qb = pack<T>(sub(E, O));
             store_pop<T, QG, G_SW, EDGE>(lg, n, i, qa);
             store_pop<T, QG, G_SW, EDGE>(lg, n, i + 1, qb);
-            gsum = add(gsum, add(unpack<T>(qa), unpack<T>(qb)));
+            if constexpr (!F32 && LBM_PAIR_MIXED) gsum = madd2<T>(qb, madd2<T>(qa, gsum));
+            else gsum = add(gsum, add(unpack<T>(qa), unpack<T>(qb)));
         }
         if constexpr (!F32) gsum = mul(gsum, p.g_inv_scale);
         store_rest(lg.rest, n, sub(M.ps, gsum));
@@ -549,7 +630,9 @@ __device__ __forceinline__ void collide2(const Params &p, const Lat<T> &lh, cons
         const P qa = pack<T>(a), qb = pack<T>(b);
         store_pop<T, QP, H_SW, EDGE>(lh, n, i, qa);
         store_pop<T, QP, H_SW, EDGE>(lh, n, i + 1, qb);
-        dsum = add(dsum, add(sub(unpack<T>(qa), hv[i]), sub(unpack<T>(qb), hv[i + 1])));
+        // the mass increments q*_i - q_i, exact in FP32 (differences of 16-bit values)
+        if constexpr (!F32 && LBM_PAIR_MIXED) dsum = add(dsum, add(msub2<T>(qa, hv[i]), msub2<T>(qb, hv[i + 1])));
+        else dsum = add(dsum, add(sub(unpack<T>(qa), hv[i]), sub(unpack<T>(qb), hv[i + 1])));
     }
     store_rest(lh.rest, n, sub(hv[0], dsum));
 }
