@@ -179,7 +179,11 @@ lbm_status lbm_create(lbm_t **out, const lbm_domain *dom, const lbm_params *prm,
 lbm_status lbm_init_phase(lbm_t *s, const float *phi0, int phi0_on_device);
 
 /* Advances n >= 0 coupled time steps (Algorithm 2: phase step, hydro step).
- * Asynchronous: returns after enqueueing. */
+ * Asynchronous: returns after enqueueing.  On a stream of its own (not NULL) and
+ * for boxes of at most 8,388,608 cells, runs of 16 steps are replayed from CUDA
+ * graphs captured on first use (one per starting AA parity and phi buffer, kept
+ * until lbm_destroy), so the first call with n >= 16 takes longer; while the
+ * stream is being captured by the caller, every step is launched directly. */
 lbm_status lbm_step(lbm_t *s, int64_t n);
 
 /* Macroscopic fields at the current time level t: phi = sum_i h_i

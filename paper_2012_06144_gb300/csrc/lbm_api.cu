@@ -199,6 +199,62 @@ size_t plane_bytes(const lbm_t *s) { return (size_t)s->kp.N * sizeof(float); }
 
 cudaMemcpyKind kind_to_device(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 
+// One time step's launch(es) at the handle's current level.
+cudaError_t enqueue_one(lbm_t *s) {
+    if (s->unfused)
+        return lbm::launch_unfused(s->kp, s->uf, s->sto, s->dom.q_hydro, true, s->phi[s->cur], s->phi[s->cur ^ 1],
+                                   s->flag, s->stream);
+    return lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, s->dom.q_phase, g_swapped(s), h_swapped(s), true,
+                            s->phi[s->cur], s->phi[s->cur ^ 1], s->flag, s->stream);
+}
+
+// Small boxes spend most of a step launching it: runs of kStepGraph steps are
+// replayed from a CUDA graph (captured on first use, one per starting parity and
+// phi buffer) when the handle has its own stream that nobody is capturing.
+constexpr int kStepGraph = 16;
+constexpr long long kStepGraphCells = 1ll << 23;  // boxes up to 8 M cells
+
+lbm_status step_graph_for(lbm_t *s, cudaGraphExec_t *out) {
+    const int key = (int)((s->t & 1) * 2 + s->cur);
+    if (!s->step_graph[key]) {
+        const int64_t t0 = s->t;
+        const int c0 = s->cur;
+        cudaGraph_t g = nullptr;
+        LBM_CK(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < kStepGraph && e == cudaSuccess; ++k) {
+            e = enqueue_one(s);
+            s->cur ^= 1;
+            s->t += 1;
+        }
+        s->t = t0;  // capture enqueues nothing: the level stays until the graph runs
+        s->cur = c0;
+        const cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
+        if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&s->step_graph[key], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            s->step_graph[key] = nullptr;
+            return cuda_fail(s, e != cudaSuccess ? e : e2, "step graph capture");
+        }
+    }
+    *out = s->step_graph[key];
+    return LBM_OK;
+}
+
+bool step_graphs_apply(const lbm_t *s) {
+    if (!s->stream || s->kp.N > kStepGraphCells) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+}
+
+void drop_step_graphs(lbm_t *s) {
+    for (auto &g : s->step_graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
 }  // namespace
 
 namespace lbm {
@@ -325,15 +381,22 @@ lbm_status lbm_step(lbm_t *s, int64_t n) {
     if (!s || n < 0) return LBM_ERR_ARG;
     if (!s->ready) return s->err = "lbm_step before lbm_init_phase / lbm_set_state", LBM_ERR_STATE;
     DeviceGuard dg(s->device);
-    for (int64_t k = 0; k < n; ++k) {
-        if (s->unfused)
-            LBM_CK(s, lbm::launch_unfused(s->kp, s->uf, s->sto, s->dom.q_hydro, true, s->phi[s->cur],
-                                          s->phi[s->cur ^ 1], s->flag, s->stream));
-        else
-            LBM_CK(s, lbm::launch_step(s->kp, s->sto, s->dom.q_hydro, s->dom.q_phase, g_swapped(s), h_swapped(s), true,
-                                       s->phi[s->cur], s->phi[s->cur ^ 1], s->flag, s->stream));
-        s->cur ^= 1;
-        s->t += 1;
+    const bool graphs = n >= kStepGraph && step_graphs_apply(s);
+    while (n > 0) {
+        if (graphs && n >= kStepGraph) {
+            cudaGraphExec_t g = nullptr;
+            const lbm_status st = step_graph_for(s, &g);
+            if (st != LBM_OK) return st;
+            LBM_CK(s, cudaGraphLaunch(g, s->stream));
+            s->cur ^= kStepGraph & 1;
+            s->t += kStepGraph;
+            n -= kStepGraph;
+        } else {
+            LBM_CK(s, enqueue_one(s));
+            s->cur ^= 1;
+            s->t += 1;
+            n -= 1;
+        }
     }
     return LBM_OK;
 }
@@ -454,6 +517,7 @@ void lbm_destroy(lbm_t *s) {
     {
         DeviceGuard dg(s->device);
         cudaStreamSynchronize(s->stream);
+        drop_step_graphs(s);
         if (s->owns_ws) cudaFree(s->ws);
     }
     delete s;

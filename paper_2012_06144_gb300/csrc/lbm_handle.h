@@ -27,6 +27,9 @@ struct lbm_t {
     int64_t t;    // time level: steps advanced since initialisation
     bool ready;   // a state exists
     std::string err;
+    // runs of kStepGraph steps of small boxes replayed from CUDA graphs, by the
+    // AA parity of the first step and the phi buffer it reads ((t & 1) * 2 + cur)
+    cudaGraphExec_t step_graph[4];
 };
 
 namespace lbm {
