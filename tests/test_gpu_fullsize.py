@@ -191,3 +191,49 @@ def test_rising_bubble_walled_sampled_parity(lbm, orc):
     sim.synchronize()
     del sim
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_storage_formats_timing_box_sampled_parity(lbm, orc, prec):
+    """The storage formats' timing box as the benchmark runs it (512^3, walls on
+    every face, D = 32 at (256, 64, 256), 16-bit moving populations): after 10
+    steps, one step at sampled cells (random, the bubble's interface, faces,
+    edges, corners) against the oracle stepping walled / periodic 5^3 patches of
+    the decoded state.  Each stored population rounds once (unit roundoff u of
+    the format); the rest populations carry the others' rounding."""
+    import torch
+
+    unit = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}[prec]
+    prob, phi0 = W.precision_timing(512)
+    sim = lbm.Simulation.from_problem(prob, precision=prec)
+    sim.init_phase(torch.from_numpy(phi0).cuda())
+    sim.step(10)
+    h0, g0, f0 = sim.get_state(on_device=True)
+    sim.step(1)
+    h1, g1, f1 = sim.get_state(on_device=True)
+    rng = np.random.default_rng(512)
+    n = 512
+    cells = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(16)]
+    cells += [(256, 64 + 16, 256), (256, 64, 256 + 16), (256 - 16, 64, 256)]
+    cells += [(0, 0, 0), (n - 1, n - 1, n - 1), (1, 300, n - 2), (n - 1, 0, 100), (200, n - 1, 0)]
+    for z, y, x in cells:
+        hp, (cz, cy, cx), pw = wall_patch(h0, (z, y, x), prob)
+        gp, _, _ = wall_patch(g0, (z, y, x), prob)
+        fp, _, _ = wall_patch(f0, (z, y, x), prob)
+        sub = W.Problem(5, 5, 5, wall=pw, q_hydro=prob.q_hydro, rho_H=prob.rho_H, rho_ratio=prob.rho_ratio,
+                        nu_H=prob.nu_H, mu_ratio=prob.mu_ratio, sigma=prob.sigma, xi=prob.xi,
+                        mobility=prob.mobility, gravity=prob.gravity, rho_ref=prob.rho_ref, clamp_phi=prob.clamp_phi)
+        p = orc.make_problem(sub)
+        g_next, u = orc.hydro_step(p, gp, fp)
+        h_next, phi_next = orc.phase_step(p, hp, fp, u)
+        rh, rg, rf = h_next[:, cz, cy, cx], g_next[:, cz, cy, cx], phi_next[cz, cy, cx]
+        got_h = h1[:, z, y, x].double().cpu().numpy()
+        got_g = g1[:, z, y, x].double().cpu().numpy()
+        # stored h_i - w_i phi_ref rounds once (phi_ref = 1): |stored| <= |h_i| + w_i
+        assert abs(float(f1[z, y, x]) - rf) <= 1e-5 * max(abs(rf), 1e-2), (z, y, x)
+        assert np.abs(got_h - rh).max() <= 15 * unit * (np.abs(rh).max() + 1.0) + 1e-5 * np.abs(rh).max(), (z, y, x)
+        assert np.abs(got_g - rg).max() <= prob.q_hydro * unit * np.abs(rg).max() + 1e-5 * np.abs(rg).max() + 1e-9, (z, y, x)
+    sim.synchronize()
+    del sim
+    torch.cuda.empty_cache()
+
