@@ -81,8 +81,8 @@ enum { LBM_PHASE_SRT = 0, LBM_PHASE_MRT = 1 };
 /* Kernel form of a time step.  FUSED: one kernel per step (Algorithm 2 with the
  * hydro(k-1) + phase(k) bracketing, in-place AA streaming, one copy of each
  * lattice: 344 B moved per cell at D3Q27), in the variant the library measured
- * faster for the storage format (FUSED_PAIR for FP16 and BF16 where it applies,
- * FUSED_CELL otherwise).  UNFUSED: the passes of the paper's straightforward
+ * faster: FUSED_PAIR wherever it applies, for every storage format, FUSED_CELL
+ * otherwise.  UNFUSED: the passes of the paper's straightforward
  * Algorithm 1 -- a collision kernel for each lattice (storing u and phi) and a
  * streaming kernel for each, over two grids (708 B per cell at D3Q27) --
  * computing the same update; the baseline the fused form is measured against
