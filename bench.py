@@ -402,10 +402,10 @@ def batched_form(args, stream, peak):
 
 def pattern_ceiling(size: int, achieved: float):
     """The bandwidth of the step's data movement without its arithmetic, from the
-    stand-alone pattern_probe program: 42 FP32 planes moved under the fused
-    kernel's AA pattern (one lattice natural, the other swapped), next to a plain
-    copy and the other streaming schemes.  frac = the kernel's achieved
-    (algorithmic) GB/s over that ceiling."""
+    stand-alone pattern_probe program: the two-cell step's accesses in FP32 under
+    both AA layouts (one lattice natural, the other swapped), next to a plain
+    copy, the one-cell AA pattern and the other streaming schemes.  frac = the
+    kernel's achieved (algorithmic) GB/s over that ceiling."""
     from paper_2012_06144_gb300 import _build
 
     if size < 32 or size > 512 or size & (size - 1):
@@ -415,8 +415,35 @@ def pattern_ceiling(size: int, achieved: float):
         probe = json.loads(r.stdout.strip().splitlines()[-1])
     except Exception as exc:  # reported, not fatal: the ceiling is context for the roofline
         return {"error": str(exc)[:200]}
+    # the two-cell step alternates its two AA layouts: the ceiling of a step pair is
+    # the harmonic mean of the two layouts' bandwidths
+    if "pair32_g_natural" in probe and "pair32_g_swapped" in probe:
+        gbs = 2.0 / (1.0 / probe["pair32_g_natural"] + 1.0 / probe["pair32_g_swapped"])
+        return {"pattern": "the two-cell step's accesses (two cells per thread, aligned pairs where the AA "
+                           "layout allows, FP32, no arithmetic), both AA layouts",
+                "gbs": gbs, "frac": achieved / gbs, "aa_one_cell_gbs": probe["aa_mix"], "probe": probe}
     return {"pattern": "AA: one lattice natural, the other swapped (42 FP32 planes, no arithmetic)",
             "gbs": probe["aa_mix"], "frac": achieved / probe["aa_mix"], "probe": probe}
+
+
+def pattern_ceiling_16bit(probe, forms):
+    """The bandwidth of the two-cell step's data movement with 16-bit moving
+    populations and no arithmetic (pattern_probe's pair16 modes, one per AA
+    layout; a step alternates them, so the ceiling is their harmonic mean), and
+    the 16-bit forms' achieved (algorithmic) GB/s over it."""
+    try:
+        nat, sw = probe["pair16_g_natural"], probe["pair16_g_swapped"]
+    except (TypeError, KeyError):
+        return None
+    gbs = 2.0 / (1.0 / nat + 1.0 / sw)
+    out = {"pattern": "two cells per thread, 16-bit moving populations (one scalar access per cell for the "
+                      "swapped lattice's x-moving populations), periodic box, no arithmetic",
+           "gbs": gbs, "g_natural": nat, "g_swapped": sw}
+    for k in ("fp16", "bf16"):
+        f = forms.get(k)
+        if isinstance(f, dict) and "value" in f:
+            out[k + "_frac"] = f["value"] * 1e6 * f["bytes_per_cell"] / 1e9 / gbs
+    return out
 
 
 def unfused_bytes_per_cell(q: int) -> int:
@@ -669,6 +696,8 @@ def main():
     forms = None
     if rank == 0 and not args.no_precision and headline:
         forms = precision_forms(args, stream, peak)
+        if forms and isinstance(roof.get("pattern_ceiling"), dict):
+            forms["pattern_ceiling"] = pattern_ceiling_16bit(roof["pattern_ceiling"].get("probe"), forms)
     batched = None
     if rank == 0 and not args.no_batched and headline:
         batched = batched_form(args, stream, peak)

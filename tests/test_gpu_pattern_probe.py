@@ -16,5 +16,6 @@ def test_pattern_probe_reports_every_pattern():
     out = json.loads(r.stdout.strip().splitlines()[-1])
     assert out["n"] == 128 and out["planes"] == 42 and out["unit"] == "GB/s"
     assert "aa_cluster" not in out and "aa_xalign" not in out
-    for k in ("copy", "local", "aa_mix", "aa_odd", "pull", "push", "twist"):
+    for k in ("copy", "local", "aa_mix", "aa_odd", "pull", "push", "twist", "pair32_g_natural", "pair32_g_swapped",
+              "pair16_g_natural", "pair16_g_swapped"):
         assert 0.0 < out[k] < 20000.0, (k, out[k])
