@@ -20,7 +20,8 @@
 // Needs nx even (so that every pair starts on an even element and a thread's
 // two cells are both inside or both outside the box) and the 32-bit plane
 // offsets of the single-cell kernel ((q - 1) N < 2^32); the D3Q15 phase lattice
-// with the SRT collision and D3Q19 or D3Q27 hydrodynamics.
+// with the SRT collision (or, in FP32, the MRT one) and D3Q19 or D3Q27
+// hydrodynamics.
 //
 // The arithmetic follows the single-cell kernel term by term (lbm_device.cuh,
 // lbm_step_impl.cuh) with the same reformulations: stencils from opposite-pair
@@ -460,7 +461,11 @@ __device__ __forceinline__ bool finite_pair(float2 v) { return fabsf(v.x) < 1e30
 // The collision of both lattices at the pair and the streaming stores, from the
 // pre-collision populations gv (g^{k-1}, storage units), hv (h^k, storage units)
 // and the neighbourhood nb of phi^{k-1}.  See collide_and_store.
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, int EDGE>
+// PMRT: the MRT phase collision of Section 3.1 (first-order moments relaxed with
+// omega_phi, all others with 1) in the closed form of the one-cell kernel:
+// h*_i = h^eq_i + F_i / 2 + 3 (1 - omega_phi) w_i e_i . J with
+// J = sum_j e_j h_j - phi_k u + theta n / 6 (FP32 storage).
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, int EDGE, bool PMRT = false>
 __device__ __forceinline__ void collide2(const Params &p, const Lat<T> &lh, const Lat<T> &lg, const Nb4 &n,
                                          float2 grest, const typename PairOf<T>::P *gq, float2 hrest,
                                          const typename PairOf<T>::P *hq, const Stencil2 &S, float2 phic,
@@ -591,7 +596,27 @@ __device__ __forceinline__ void collide2(const Params &p, const Lat<T> &lh, cons
     const float2 theta = mul(fma2(mul(pc, -4.0f), pc, bc(1.0f)), p.inv_xi);
     // -1.5 u.u
     const float2 nuu = mul(fma2(uz, uz, fma2(uy, uy, mul(ux, ux))), -1.5f);
-    const float om = p.omega_phi, fc = 1.0f - 0.5f * om;
+    float om = p.omega_phi, fc = 1.0f - 0.5f * om;
+    float2 cJx = bc(0.f), cJy = bc(0.f), cJz = bc(0.f);
+    if constexpr (PMRT) {
+        static_assert(F32, "the MRT phase collision is built for FP32 storage");
+        float2 jx = bc(0.f), jy = bc(0.f), jz = bc(0.f);
+#pragma unroll
+        for (int i = 1; i < QP; i += 2) {
+            const V3 e = vel<QP>(i);
+            const float2 dh = sub(hv[i], hv[i + 1]);
+            if (e.x) jx = acc_signed(jx, dh, e.x);
+            if (e.y) jy = acc_signed(jy, dh, e.y);
+            if (e.z) jz = acc_signed(jz, dh, e.z);
+        }
+        const float c = 3.0f * (1.0f - om);
+        const float2 th = mul(theta, 0.5f / 3.0f);
+        cJx = mul(sub(fma2(th, nx, jx), mul(phik, ux)), c);
+        cJy = mul(sub(fma2(th, ny, jy), mul(phik, uy)), c);
+        cJz = mul(sub(fma2(th, nz, jz), mul(phik, uz)), c);
+        om = 1.0f;
+        fc = 0.5f;
+    }
     const float2 phin = F32 ? phik : sub(phik, bc(href));
     const float2 fth = mul(theta, fc);
     // per weight class c (|e|^2 = 1, 2, 3; the classes of the phase lattice):
@@ -625,8 +650,17 @@ __device__ __forceinline__ void collide2(const Params &p, const Lat<T> &lh, cons
         // then q*_i = q_i + F_i - omega (minus the non-equilibrium)
         const float2 ma = sub(fma2(phin, -w, hv[i]), add(x_even, x_odd));
         const float2 mb = sub(fma2(phin, -w, hv[i + 1]), sub(x_even, x_odd));
-        const float2 a = fma2(ma, -om, add(hv[i], F));
-        const float2 b = fma2(mb, -om, sub(hv[i + 1], F));
+        float2 a = fma2(ma, -om, add(hv[i], F));
+        float2 b = fma2(mb, -om, sub(hv[i + 1], F));
+        if constexpr (PMRT) {  // + w_i e_i . (3 (1 - omega_phi) J), odd in e
+            float2 corr = bc(0.f);
+            if (e.x) corr = acc_signed(corr, cJx, e.x);
+            if (e.y) corr = acc_signed(corr, cJy, e.y);
+            if (e.z) corr = acc_signed(corr, cJz, e.z);
+            corr = mul(corr, w);
+            a = add(a, corr);
+            b = sub(b, corr);
+        }
         const P qa = pack<T>(a), qb = pack<T>(b);
         store_pop<T, QP, H_SW, EDGE>(lh, n, i, qa);
         store_pop<T, QP, H_SW, EDGE>(lh, n, i + 1, qb);
@@ -644,7 +678,7 @@ struct PairShape {
     static constexpr int PXT = 2 * TXT, ROWT = 2 * TXT + 4, NT = TXT * TYT * TZT;
 };
 
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, int EDGE, int TXT, int TYT, int TZT>
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, int EDGE, int TXT, int TYT, int TZT, bool PMRT = false>
 __device__ __forceinline__ void pair_cells(const Params &p, const Lat<T> &lh, const Lat<T> &lg, const Nb4 &n,
                                            bool active, const float *__restrict__ phi_in,
                                            float (*tile)[TYT + 2][2 * TXT + 4], float *__restrict__ phi_out,
@@ -733,7 +767,7 @@ __device__ __forceinline__ void pair_cells(const Params &p, const Lat<T> &lh, co
     float2 phic;
     const Stencil2 S = stencil_from_tile<PLANE>(
         [&](int dy, int dz) { return &tile[PLANE ? 1 : tz + 1 + dz][ty + 1 + dy][2 * tx]; }, phic);
-    collide2<T, QG, QP, G_SW, H_SW, EDGE>(p, lh, lg, n, grest, gq, hrest, hq, S, phic, phi_out, flag);
+    collide2<T, QG, QP, G_SW, H_SW, EDGE, PMRT>(p, lh, lg, n, grest, gq, hrest, hq, S, phic, phi_out, flag);
 }
 
 // One tile (bx, by, bz) of 2 TXT x TYT x TZT cells of a box, one thread per pair
@@ -742,7 +776,7 @@ __device__ __forceinline__ void pair_cells(const Params &p, const Lat<T> &lh, co
 // those alone, as the batch's walled boxes at most 64 cells wide mostly need).
 // Every thread of the block must call this (it synchronises).
 template <typename T, int QG, int QP, bool G_SW, bool H_SW, int TXT = TX, int TYT = TY, int TZT = TZ,
-          bool XONLY = false>
+          bool XONLY = false, bool PMRT = false>
 __device__ __forceinline__ void pair_tile(const Params &p, const Lat<T> &lh, const Lat<T> &lg,
                                           const float *__restrict__ phi_in, float *__restrict__ phi_out,
                                           int *__restrict__ flag, float (*tile)[TYT + 2][2 * TXT + 4], int bx,
@@ -777,13 +811,13 @@ __device__ __forceinline__ void pair_tile(const Params &p, const Lat<T> &lh, con
     const bool ex = wx && (bx == 0 || (bx + 1) * PXT >= p.nx), ey = wy && (by == 0 || (by + 1) * TYT >= p.ny),
                ez = wz && (bz == 0 || (bz + 1) * TZT >= p.nz);
     if (!(ex || ey || ez))
-        pair_cells<T, QG, QP, G_SW, H_SW, 0, TXT, TYT, TZT>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+        pair_cells<T, QG, QP, G_SW, H_SW, 0, TXT, TYT, TZT, PMRT>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
                                                             by, bz, tx, ty, tz);
     else if (XONLY && !(ey || ez))
-        pair_cells<T, QG, QP, G_SW, H_SW, 1, TXT, TYT, TZT>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+        pair_cells<T, QG, QP, G_SW, H_SW, 1, TXT, TYT, TZT, PMRT>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
                                                             by, bz, tx, ty, tz);
     else
-        pair_cells<T, QG, QP, G_SW, H_SW, 7, TXT, TYT, TZT>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+        pair_cells<T, QG, QP, G_SW, H_SW, 7, TXT, TYT, TZT, PMRT>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
                                                             by, bz, tx, ty, tz);
 }
 

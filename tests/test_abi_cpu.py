@@ -108,11 +108,10 @@ def test_invalid_params_rejected(lbm, field, value):
 @pytest.mark.parametrize("dom,prm", [
     (dict(nx=7), {}),  # nx odd: a thread's two cells would straddle rows
     (dict(nx=9, nz=1, q_phase=9, q_hydro=9), {}),
-    ({}, dict(phase_collision=1)),
 ])
 def test_pair_form_rejected_where_it_does_not_apply(lbm, dom, prm):
-    """The two-cell fused step needs nx even and the SRT phase collision: other
-    problems are refused before any launch."""
+    """The two-cell fused step needs nx even: other problems are refused before
+    any launch."""
     args = dict(nx=8, ny=8, nz=8, q_hydro=27, q_phase=15)
     args.update(dom)
     d = lbm.make_domain(args["nx"], args["ny"], args["nz"], q_hydro=args["q_hydro"], q_phase=args["q_phase"])
