@@ -90,9 +90,9 @@ enum { LBM_PHASE_SRT = 0, LBM_PHASE_MRT = 1 };
  * FUSED_CELL: the fused step with one cell per thread.  FUSED_PAIR: the fused
  * step with two neighbouring cells (x, x + 1) per thread, their arithmetic in
  * packed FP32 pairs and their population pairs moved by one access where they
- * are neighbours in memory; needs nx even and (max(q_phase, q_hydro) - 1) nx ny
- * nz < 2^32, and takes every lattice pair and both phase collisions that the
- * problem allows otherwise.  All fused variants compute
+ * are neighbours in memory; needs nx even, and takes every lattice pair, phase
+ * collision and box size that the problem allows otherwise.  All fused variants
+ * compute
  * the same update; they differ in rounding only where a multiply and an add
  * are fused differently. */
 enum { LBM_FORM_FUSED = 0, LBM_FORM_UNFUSED = 1, LBM_FORM_FUSED_CELL = 2, LBM_FORM_FUSED_PAIR = 3 };

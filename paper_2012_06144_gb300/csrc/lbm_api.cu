@@ -106,9 +106,8 @@ lbm_status validate(const lbm_domain *d, const lbm_params *p, std::string &why) 
         return why = "kernel_form must be LBM_FORM_FUSED, _UNFUSED, _FUSED_CELL or _FUSED_PAIR", LBM_ERR_ARG;
     if (p->kernel_form == LBM_FORM_UNFUSED && p->precision != LBM_PRECISION_FP32)
         return why = "the unfused form is built for FP32 storage", LBM_ERR_ARG;
-    if (p->kernel_form == LBM_FORM_FUSED_PAIR &&
-        (d->nx % 2 != 0 || !lbm::offsets32((long long)d->nx * d->ny * d->nz, d->q_hydro, d->q_phase)))
-        return why = "the two-cell fused step needs nx even and (max(q) - 1) nx ny nz < 2^32", LBM_ERR_ARG;
+    if (p->kernel_form == LBM_FORM_FUSED_PAIR && d->nx % 2 != 0)
+        return why = "the two-cell fused step needs nx even", LBM_ERR_ARG;
     if (d->q_phase != 15 && (p->precision != LBM_PRECISION_FP32 || p->phase_collision != LBM_PHASE_SRT ||
                              p->kernel_form == LBM_FORM_UNFUSED))
         return why = "the D2Q9 / D3Q19 / D3Q27 phase lattices run with FP32 storage, SRT, fused form", LBM_ERR_ARG;

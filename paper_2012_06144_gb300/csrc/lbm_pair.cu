@@ -28,9 +28,10 @@ constexpr int pair_ty() { return QP == 9 ? LBM_PAIR_TY2D : TY; }
 template <int QP>
 constexpr int pair_tz() { return QP == 9 ? 1 : TZ; }
 
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool PMRT = false>
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool PMRT = false, bool W64 = false>
 __global__ void __launch_bounds__(TX *pair_ty<QP>() * pair_tz<QP>(), pair_min_blocks<QG, QP>())
-    pair_step_kernel(Params p, Lat<T> lh, Lat<T> lg, const float *__restrict__ phi_in, float *__restrict__ phi_out,
+    pair_step_kernel(Params p, Lat<T, W64> lh, Lat<T, W64> lg, const float *__restrict__ phi_in,
+                     float *__restrict__ phi_out,
                      int *__restrict__ flag) {
     constexpr int TYk = pair_ty<QP>(), TZk = pair_tz<QP>();
     __shared__ __align__(16) float tile[TZk + 2][TYk + 2][ROW];
@@ -41,28 +42,28 @@ __global__ void __launch_bounds__(TX *pair_ty<QP>() * pair_tz<QP>(), pair_min_bl
                                                                 blockIdx.y);
 }
 
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool PMRT = false>
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool PMRT = false, bool W64 = false>
 cudaError_t launch_pair(const Params &p, const Storage &sto, const float *pi, float *po, int *flag,
                         cudaStream_t st) {
-    const Lat<T> lh{sto.h.rest, static_cast<T *>(sto.h.mov), (unsigned)p.N};
-    const Lat<T> lg{sto.g.rest, static_cast<T *>(sto.g.mov), (unsigned)p.N};
+    const Lat<T, W64> lh{sto.h.rest, static_cast<T *>(sto.h.mov), (unsigned)p.N};
+    const Lat<T, W64> lg{sto.g.rest, static_cast<T *>(sto.g.mov), (unsigned)p.N};
     constexpr int TYk = pair_ty<QP>(), TZk = pair_tz<QP>();
     const dim3 block(TX, TYk, TZk);
     const dim3 grid(((p.nx + PX - 1) / PX) * ((p.ny + TYk - 1) / TYk), (p.nz + TZk - 1) / TZk);
-    pair_step_kernel<T, QG, QP, G_SW, H_SW, PMRT><<<grid, block, 0, st>>>(p, lh, lg, pi, po, flag);
+    pair_step_kernel<T, QG, QP, G_SW, H_SW, PMRT, W64><<<grid, block, 0, st>>>(p, lh, lg, pi, po, flag);
     return cudaGetLastError();
 }
 
-template <typename T, int QP, bool PMRT = false>
+template <typename T, int QP, bool PMRT = false, bool W64 = false>
 cudaError_t launch_pair_layouts(const Params &p, const Storage &sto, int q_hydro, bool g_sw, bool h_sw,
                                 const float *pi, float *po, int *flag, cudaStream_t st) {
     if (g_sw == h_sw) return cudaErrorInvalidValue;
     if (q_hydro == 27)
-        return g_sw ? launch_pair<T, 27, QP, true, false, PMRT>(p, sto, pi, po, flag, st)
-                    : launch_pair<T, 27, QP, false, true, PMRT>(p, sto, pi, po, flag, st);
+        return g_sw ? launch_pair<T, 27, QP, true, false, PMRT, W64>(p, sto, pi, po, flag, st)
+                    : launch_pair<T, 27, QP, false, true, PMRT, W64>(p, sto, pi, po, flag, st);
     if (q_hydro == 19)
-        return g_sw ? launch_pair<T, 19, QP, true, false, PMRT>(p, sto, pi, po, flag, st)
-                    : launch_pair<T, 19, QP, false, true, PMRT>(p, sto, pi, po, flag, st);
+        return g_sw ? launch_pair<T, 19, QP, true, false, PMRT, W64>(p, sto, pi, po, flag, st)
+                    : launch_pair<T, 19, QP, false, true, PMRT, W64>(p, sto, pi, po, flag, st);
     return cudaErrorInvalidValue;
 }
 
@@ -86,9 +87,11 @@ bool pair_step_applies(const Params &p, int q_hydro, int q_phase, int precision)
     const bool lat_ok = (q_phase == 15 && (q_hydro == 19 || q_hydro == 27)) ||
                         ((q_phase == 19 || q_phase == 27) && (q_hydro == 19 || q_hydro == 27) && f32) ||
                         (q_phase == 9 && q_hydro == 9 && f32);
-    // the MRT phase collision: FP32 storage with the D3Q15 phase lattice
+    // the MRT phase collision: FP32 storage with the D3Q15 phase lattice; plane
+    // offsets beyond 32 bits: FP32 storage with the D3Q15 phase lattice (64-bit offsets)
     const bool coll_ok = !p.phase_mrt || (f32 && q_phase == 15);
-    return lat_ok && coll_ok && (p.nx % 2) == 0 && offsets32(p.N, q_hydro, q_phase);
+    const bool size_ok = offsets32(p.N, q_hydro, q_phase) || (f32 && q_phase == 15);
+    return lat_ok && coll_ok && size_ok && (p.nx % 2) == 0;
 }
 
 cudaError_t launch_pair_step(const Params &p, const Storage &sto, int q_hydro, int q_phase, bool g_sw, bool h_sw,
@@ -104,6 +107,11 @@ cudaError_t launch_pair_step(const Params &p, const Storage &sto, int q_hydro, i
     }
     switch (sto.precision) {
         case LBM_PRECISION_FP32:
+            if (!offsets32(p.N, q_hydro, q_phase))
+                return p.phase_mrt ? pairstep::launch_pair_layouts<float, 15, true, true>(p, sto, q_hydro, g_sw, h_sw,
+                                                                                         phi_in, phi_out, flag, st)
+                                   : pairstep::launch_pair_layouts<float, 15, false, true>(p, sto, q_hydro, g_sw, h_sw,
+                                                                                          phi_in, phi_out, flag, st);
             if (p.phase_mrt)
                 return pairstep::launch_pair_layouts<float, 15, true>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out,
                                                                       flag, st);

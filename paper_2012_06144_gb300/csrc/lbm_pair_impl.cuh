@@ -18,10 +18,10 @@
 //     x + 1 - e_x straddle two aligned pairs or wrap around the box) take one
 //     access per cell.
 // Needs nx even (so that every pair starts on an even element and a thread's
-// two cells are both inside or both outside the box) and the 32-bit plane
-// offsets of the single-cell kernel ((q - 1) N < 2^32); the D3Q15 phase lattice
-// with the SRT collision (or, in FP32, the MRT one) and D3Q19 or D3Q27
-// hydrodynamics.
+// two cells are both inside or both outside the box); plane offsets in 32 bits
+// ((q - 1) N < 2^32) or, for larger FP32 boxes, in 64 bits; the D3Q15 phase
+// lattice with the SRT collision (or, in FP32, the MRT one) and D3Q19 or D3Q27
+// hydrodynamics (and, in FP32, the other lattice pairs of Section 5.1).
 //
 // The arithmetic follows the single-cell kernel term by term (lbm_device.cuh,
 // lbm_step_impl.cuh) with the same reformulations: stencils from opposite-pair
@@ -151,14 +151,17 @@ __device__ __forceinline__ float2 msub2(typename PairOf<T>::P q, float2 c) {
     return make_float2(msub<T>(lo<T>(q), c.x), msub<T>(hi<T>(q), c.y));
 }
 
-// One lattice: FP32 rest plane and q - 1 moving planes of type T, 32-bit element
-// offsets (s - 1) N + idx.
-template <typename T>
+// One lattice: FP32 rest plane and q - 1 moving planes of type T, element offsets
+// (s - 1) N + idx in 32 bits, or (W64) in 64 bits for boxes with (q - 1) N >= 2^32.
+template <typename T, bool W64 = false>
 struct Lat {
     float *rest;
     T *mov;
     unsigned N;
-    __device__ __forceinline__ T *at(int s, int idx) const { return mov + ((unsigned)(s - 1) * N + (unsigned)idx); }
+    __device__ __forceinline__ T *at(int s, int idx) const {
+        if constexpr (W64) return mov + ((size_t)(s - 1) * N + (size_t)(unsigned)idx);
+        else return mov + ((unsigned)(s - 1) * N + (unsigned)idx);
+    }
 };
 
 // Per-thread offsets of the pair: X[k] is the element index of x - 1 + k in the
@@ -222,8 +225,8 @@ __device__ __forceinline__ constexpr bool paired(int i) {
 // Pre-collision moving population f_i (i > 0) of both cells as stored (a
 // packed pair of the storage type; converted where it is used, so that the
 // loaded state occupies one register per population pair in 16-bit storage).
-template <typename T, int Q, bool SW, int EDGE>
-__device__ __forceinline__ typename PairOf<T>::P load_pop(const Lat<T> &L, const Nb4 &n, int i) {
+template <typename T, int Q, bool SW, int EDGE, bool W64 = false>
+__device__ __forceinline__ typename PairOf<T>::P load_pop(const Lat<T, W64> &L, const Nb4 &n, int i) {
     using P = typename PairOf<T>::P;
     if (paired<Q, SW>(i)) {
         int slot, idx;
@@ -242,8 +245,8 @@ __device__ __forceinline__ float2 load_rest(const float *rest, const Nb4 &n) {
 }
 
 // Stores the encoded post-collision f*_i of both cells.
-template <typename T, int Q, bool SW, int EDGE>
-__device__ __forceinline__ void store_pop(const Lat<T> &L, const Nb4 &n, int i, typename PairOf<T>::P v) {
+template <typename T, int Q, bool SW, int EDGE, bool W64 = false>
+__device__ __forceinline__ void store_pop(const Lat<T, W64> &L, const Nb4 &n, int i, typename PairOf<T>::P v) {
     using P = typename PairOf<T>::P;
     if (paired<Q, SW>(i)) {
         int slot, idx;
@@ -465,8 +468,8 @@ __device__ __forceinline__ bool finite_pair(float2 v) { return fabsf(v.x) < 1e30
 // omega_phi, all others with 1) in the closed form of the one-cell kernel:
 // h*_i = h^eq_i + F_i / 2 + 3 (1 - omega_phi) w_i e_i . J with
 // J = sum_j e_j h_j - phi_k u + theta n / 6 (FP32 storage).
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, int EDGE, bool PMRT = false>
-__device__ __forceinline__ void collide2(const Params &p, const Lat<T> &lh, const Lat<T> &lg, const Nb4 &n,
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, int EDGE, bool PMRT = false, bool W64 = false>
+__device__ __forceinline__ void collide2(const Params &p, const Lat<T, W64> &lh, const Lat<T, W64> &lg, const Nb4 &n,
                                          float2 grest, const typename PairOf<T>::P *gq, float2 hrest,
                                          const typename PairOf<T>::P *hq, const Stencil2 &S, float2 phic,
                                          float *__restrict__ phi_out, int *__restrict__ flag) {
@@ -678,8 +681,9 @@ struct PairShape {
     static constexpr int PXT = 2 * TXT, ROWT = 2 * TXT + 4, NT = TXT * TYT * TZT;
 };
 
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, int EDGE, int TXT, int TYT, int TZT, bool PMRT = false>
-__device__ __forceinline__ void pair_cells(const Params &p, const Lat<T> &lh, const Lat<T> &lg, const Nb4 &n,
+template <typename T, int QG, int QP, bool G_SW, bool H_SW, int EDGE, int TXT, int TYT, int TZT, bool PMRT = false,
+          bool W64 = false>
+__device__ __forceinline__ void pair_cells(const Params &p, const Lat<T, W64> &lh, const Lat<T, W64> &lg, const Nb4 &n,
                                            bool active, const float *__restrict__ phi_in,
                                            float (*tile)[TYT + 2][2 * TXT + 4], float *__restrict__ phi_out,
                                            int *__restrict__ flag, int bx, int by, int bz, int tx, int ty, int tz) {
@@ -767,7 +771,7 @@ __device__ __forceinline__ void pair_cells(const Params &p, const Lat<T> &lh, co
     float2 phic;
     const Stencil2 S = stencil_from_tile<PLANE>(
         [&](int dy, int dz) { return &tile[PLANE ? 1 : tz + 1 + dz][ty + 1 + dy][2 * tx]; }, phic);
-    collide2<T, QG, QP, G_SW, H_SW, EDGE, PMRT>(p, lh, lg, n, grest, gq, hrest, hq, S, phic, phi_out, flag);
+    collide2<T, QG, QP, G_SW, H_SW, EDGE, PMRT, W64>(p, lh, lg, n, grest, gq, hrest, hq, S, phic, phi_out, flag);
 }
 
 // One tile (bx, by, bz) of 2 TXT x TYT x TZT cells of a box, one thread per pair
@@ -776,8 +780,8 @@ __device__ __forceinline__ void pair_cells(const Params &p, const Lat<T> &lh, co
 // those alone, as the batch's walled boxes at most 64 cells wide mostly need).
 // Every thread of the block must call this (it synchronises).
 template <typename T, int QG, int QP, bool G_SW, bool H_SW, int TXT = TX, int TYT = TY, int TZT = TZ,
-          bool XONLY = false, bool PMRT = false>
-__device__ __forceinline__ void pair_tile(const Params &p, const Lat<T> &lh, const Lat<T> &lg,
+          bool XONLY = false, bool PMRT = false, bool W64 = false>
+__device__ __forceinline__ void pair_tile(const Params &p, const Lat<T, W64> &lh, const Lat<T, W64> &lg,
                                           const float *__restrict__ phi_in, float *__restrict__ phi_out,
                                           int *__restrict__ flag, float (*tile)[TYT + 2][2 * TXT + 4], int bx,
                                           int by, int bz) {
@@ -811,13 +815,13 @@ __device__ __forceinline__ void pair_tile(const Params &p, const Lat<T> &lh, con
     const bool ex = wx && (bx == 0 || (bx + 1) * PXT >= p.nx), ey = wy && (by == 0 || (by + 1) * TYT >= p.ny),
                ez = wz && (bz == 0 || (bz + 1) * TZT >= p.nz);
     if (!(ex || ey || ez))
-        pair_cells<T, QG, QP, G_SW, H_SW, 0, TXT, TYT, TZT, PMRT>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+        pair_cells<T, QG, QP, G_SW, H_SW, 0, TXT, TYT, TZT, PMRT, W64>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
                                                             by, bz, tx, ty, tz);
     else if (XONLY && !(ey || ez))
-        pair_cells<T, QG, QP, G_SW, H_SW, 1, TXT, TYT, TZT, PMRT>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+        pair_cells<T, QG, QP, G_SW, H_SW, 1, TXT, TYT, TZT, PMRT, W64>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
                                                             by, bz, tx, ty, tz);
     else
-        pair_cells<T, QG, QP, G_SW, H_SW, 7, TXT, TYT, TZT, PMRT>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
+        pair_cells<T, QG, QP, G_SW, H_SW, 7, TXT, TYT, TZT, PMRT, W64>(p, lh, lg, n, active, phi_in, tile, phi_out, flag, bx,
                                                             by, bz, tx, ty, tz);
 }
 

@@ -137,10 +137,12 @@ def test_roofline_512_mass_and_finiteness(lbm):
     torch.cuda.empty_cache()
 
 
-def test_beyond_32bit_offsets_sampled_parity(lbm, orc):
+@pytest.mark.parametrize("form", ["fused", "cell"])
+def test_beyond_32bit_offsets_sampled_parity(lbm, orc, form):
     """A box whose moving-plane offsets exceed 32 bits (26 N >= 2^32: 576 x 576 x 544,
-    180 M cells) runs the 64-bit plane-pointer form of the fused kernel; sampled
-    one-step parity in both in-place layouts, as for the 512^3 benchmark box."""
+    180 M cells) runs the fused step with 64-bit plane offsets (two cells per
+    thread) or 64-bit plane pointers (one cell per thread); sampled one-step parity
+    in both in-place layouts, as for the 512^3 benchmark box."""
     import torch
 
     nx, ny, nz = 576, 576, 544
@@ -153,7 +155,7 @@ def test_beyond_32bit_offsets_sampled_parity(lbm, orc):
     z = torch.arange(nz, device="cuda", dtype=torch.float32) + 0.5
     phi0 = (0.5 + 0.45 * torch.sin(two_pi * x / nx)[None, None, :] * torch.sin(two_pi * 3 * y / ny)[None, :, None]
             * torch.cos(two_pi * 2 * z / nz)[:, None, None]).contiguous()
-    sim = lbm.Simulation.from_problem(prob)
+    sim = lbm.Simulation.from_problem(prob, form=form)
     sim.init_phase(phi0)
     rng = np.random.default_rng(576)
     cells = [(int(rng.integers(0, nz)), int(rng.integers(0, ny)), int(rng.integers(0, nx))) for _ in range(24)]
