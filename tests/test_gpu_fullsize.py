@@ -83,7 +83,8 @@ def check_sampled_step(lbm, orc, sim, prob, cells):
         fp, _, _ = wall_patch(phi0, (z, y, x), prob)
         sub = W.Problem(5, 5, 5, wall=pw, q_hydro=prob.q_hydro, rho_H=prob.rho_H, rho_ratio=prob.rho_ratio,
                         nu_H=prob.nu_H, mu_ratio=prob.mu_ratio, sigma=prob.sigma, xi=prob.xi,
-                        mobility=prob.mobility, gravity=prob.gravity, rho_ref=prob.rho_ref, clamp_phi=prob.clamp_phi)
+                        mobility=prob.mobility, gravity=prob.gravity, rho_ref=prob.rho_ref, clamp_phi=prob.clamp_phi,
+                        phase_mrt=prob.phase_mrt)
         p = orc.make_problem(sub)
         g_next, u = orc.hydro_step(p, gp, fp)
         h_next, phi_next = orc.phase_step(p, hp, fp, u)
@@ -137,18 +138,19 @@ def test_roofline_512_mass_and_finiteness(lbm):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("form", ["fused", "cell"])
-def test_beyond_32bit_offsets_sampled_parity(lbm, orc, form):
+@pytest.mark.parametrize("form,mrt", [("fused", 0), ("cell", 0), ("fused", 1)])
+def test_beyond_32bit_offsets_sampled_parity(lbm, orc, form, mrt):
     """A box whose moving-plane offsets exceed 32 bits (26 N >= 2^32: 576 x 576 x 544,
     180 M cells) runs the fused step with 64-bit plane offsets (two cells per
-    thread) or 64-bit plane pointers (one cell per thread); sampled one-step parity
-    in both in-place layouts, as for the 512^3 benchmark box."""
+    thread) or 64-bit plane pointers (one cell per thread), with the SRT and the
+    MRT phase collision; sampled one-step parity in both in-place layouts, as for
+    the 512^3 benchmark box."""
     import torch
 
     nx, ny, nz = 576, 576, 544
     assert 26 * nx * ny * nz >= 2 ** 32
     prob = W.Problem(nx, ny, nz, wall=(0, 0, 0), q_hydro=27, rho_ratio=100.0, sigma=1e-3, xi=4.0,
-                     gravity=(0.0, -1e-6, 0.0), rho_ref=0.5, clamp_phi=1)
+                     gravity=(0.0, -1e-6, 0.0), rho_ref=0.5, clamp_phi=1, phase_mrt=mrt)
     two_pi = 2.0 * np.pi
     x = torch.arange(nx, device="cuda", dtype=torch.float32) + 0.5
     y = torch.arange(ny, device="cuda", dtype=torch.float32) + 0.5
@@ -224,7 +226,8 @@ def test_storage_formats_timing_box_sampled_parity(lbm, orc, prec):
         fp, _, _ = wall_patch(f0, (z, y, x), prob)
         sub = W.Problem(5, 5, 5, wall=pw, q_hydro=prob.q_hydro, rho_H=prob.rho_H, rho_ratio=prob.rho_ratio,
                         nu_H=prob.nu_H, mu_ratio=prob.mu_ratio, sigma=prob.sigma, xi=prob.xi,
-                        mobility=prob.mobility, gravity=prob.gravity, rho_ref=prob.rho_ref, clamp_phi=prob.clamp_phi)
+                        mobility=prob.mobility, gravity=prob.gravity, rho_ref=prob.rho_ref, clamp_phi=prob.clamp_phi,
+                        phase_mrt=prob.phase_mrt)
         p = orc.make_problem(sub)
         g_next, u = orc.hydro_step(p, gp, fp)
         h_next, phi_next = orc.phase_step(p, hp, fp, u)
