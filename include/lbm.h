@@ -102,8 +102,8 @@ typedef struct {
     int nx, ny, nz; /* cells per axis, each >= 1, nx*ny*nz < 2^31,
                        ny <= 524280, nz <= 65535 (launch-grid limits); boxes
                        with (max(q_phase, q_hydro) - 1) nx ny nz >= 2^32 (about
-                       165 M cells at D3Q27) need FP32 storage, the SRT phase
-                       collision and the D3Q15 phase lattice                   */
+                       165 M cells at D3Q27) need FP32 storage and the D3Q15
+                       phase lattice                                           */
     int wall[3];    /* 0 = periodic axis, 1 = no-slip walls on both faces       */
     int q_phase;    /* 15 (the benchmarked pair), 19 or 27; or 9 with q_hydro 9
                        (the two-dimensional D2Q9 pair of Section 5.1: nz = 1,

@@ -114,8 +114,8 @@ lbm_status validate(const lbm_domain *d, const lbm_params *p, std::string &why) 
     if (d->q_phase == 9 && p->gravity[2] != 0.0)
         return why = "the D2Q9 pair carries no z momentum: gravity[2] must be 0", LBM_ERR_ARG;
     if (!lbm::offsets32((long long)d->nx * d->ny * d->nz, d->q_hydro, d->q_phase) &&
-        (p->precision != LBM_PRECISION_FP32 || p->phase_collision != LBM_PHASE_SRT || d->q_phase != 15))
-        return why = "boxes with (q - 1) nx ny nz >= 2^32 run with FP32 storage, SRT and the D3Q15 phase lattice",
+        (p->precision != LBM_PRECISION_FP32 || d->q_phase != 15))
+        return why = "boxes with (q - 1) nx ny nz >= 2^32 run with FP32 storage and the D3Q15 phase lattice",
                LBM_ERR_ARG;
     const double rho_L = p->rho_H / p->rho_ratio;
     const double nu_L = p->nu_H * p->rho_H / (p->mu_ratio * rho_L);

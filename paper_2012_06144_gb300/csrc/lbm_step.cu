@@ -104,8 +104,8 @@ static cudaError_t launch(const Params &p, const Planes &pl, const float *pi, fl
                           cudaStream_t st) {
     if constexpr (prefer_offsets32<T, QG, QP>()) {
         if (offsets32(p.N, QG, QP)) return launch_k<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, true>(p, pl, pi, po, flag, st);
-        // larger boxes: the pointer form, FP32 / SRT / D3Q15 only (checked on creation)
-        if constexpr (std::is_same<T, float>::value && QP == 15 && !PMRT)
+        // larger boxes: the pointer form, FP32 / D3Q15 only (checked on creation)
+        if constexpr (std::is_same<T, float>::value && QP == 15)
             return launch_k<T, QG, QP, G_SW, H_SW, HYDRO, PMRT, false>(p, pl, pi, po, flag, st);
         else
             return cudaErrorInvalidValue;

@@ -278,10 +278,12 @@ def test_d2q9_pair_limits(lbm):
 
 
 def test_large_box_limits(lbm):
-    """Beyond 32-bit plane offsets only the FP32 / SRT / D3Q15-phase form runs."""
+    """Beyond 32-bit plane offsets FP32 storage with the D3Q15 phase lattice runs
+    (SRT or MRT); 16-bit storage and the other phase lattices are refused."""
     d = lbm.make_domain(576, 576, 544, q_hydro=27)
     assert lbm.lbm_workspace_size(d, lbm.make_params()) > 0
-    for kw in (dict(precision=lbm.LBM_PRECISION_FP16), dict(phase_collision=lbm.LBM_PHASE_MRT)):
+    assert lbm.lbm_workspace_size(d, lbm.make_params(phase_collision=lbm.LBM_PHASE_MRT)) > 0
+    for kw in (dict(precision=lbm.LBM_PRECISION_FP16), dict(precision=lbm.LBM_PRECISION_BF16)):
         with pytest.raises(lbm.LBMError) as ei:
             lbm.lbm_workspace_size(d, lbm.make_params(**kw))
         assert ei.value.status == lbm.LBM_ERR_ARG

@@ -138,7 +138,7 @@ def test_roofline_512_mass_and_finiteness(lbm):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("form,mrt", [("fused", 0), ("cell", 0), ("fused", 1)])
+@pytest.mark.parametrize("form,mrt", [("fused", 0), ("cell", 0), ("fused", 1), ("cell", 1)])
 def test_beyond_32bit_offsets_sampled_parity(lbm, orc, form, mrt):
     """A box whose moving-plane offsets exceed 32 bits (26 N >= 2^32: 576 x 576 x 544,
     180 M cells) runs the fused step with 64-bit plane offsets (two cells per
