@@ -97,30 +97,6 @@ __device__ __forceinline__ void batch_tile(const GroupArgs &a, const int4 e, int
                                                                          threadIdx.y, threadIdx.z, tma);
 }
 
-#ifndef LBM_BATCH_PERSISTENT
-#define LBM_BATCH_PERSISTENT 0
-#endif
-
-#if LBM_BATCH_PERSISTENT
-// Measurement variant (built with -DLBM_BATCH_PERSISTENT=1, per-thread halo loads
-// only): a persistent grid whose blocks walk the table with a stride of the grid
-// size, the tile body behind a call so that the loop leaves its register
-// allocation alone.
-template <int QG, bool G_SW, bool H_SW, int TY, int TZ>
-__device__ __noinline__ void batch_tile_call(const GroupArgs &a, const int4 e, int cur, float (*tile)[TY + 2][TX + 2]) {
-    batch_tile<QG, G_SW, H_SW, TY, TZ, 0>(a, e, cur, tile, nullptr);
-}
-
-template <int QG, bool G_SW, bool H_SW, int TY, int TZ, int HALO>
-__global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
-    batch_step_kernel(const __grid_constant__ GroupArgs a, const int4 *__restrict__ tiles, int cur, int ntiles) {
-    __shared__ __align__(128) float tile[TZ + 2][TY + 2][TX + 2];
-    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
-        batch_tile_call<QG, G_SW, H_SW, TY, TZ>(a, tiles[k], cur, tile);
-        __syncthreads();  // every thread is done with this tile's phi before the next fill
-    }
-}
-#else
 // One block per entry tiles[blockIdx.x] = (member within the group, bx, by, bz).
 template <int QG, bool G_SW, bool H_SW, int TY, int TZ, int HALO>
 __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
@@ -130,7 +106,6 @@ __global__ void __launch_bounds__(TX *TY *TZ, LBM_MIN_BLOCKS)
     __shared__ uint64_t bar;
     batch_tile<QG, G_SW, H_SW, TY, TZ, HALO>(a, tiles[blockIdx.x], cur, tile, &bar);
 }
-#endif
 
 // The two-cell step over the table: one block of 16 x 4 x 2 threads per entry
 // (member within the group, bx, by, bz) of 32 x 4 x 2 cells.
@@ -148,19 +123,10 @@ __global__ void __launch_bounds__(kPairTX *kPairTY *kPairTZ, LBM_PAIR_MIN_BLOCKS
 template <int QG, bool G_SW, bool H_SW, int TY, int TZ>
 static cudaError_t launch_shape(int halo, const GroupArgs &a, const int4 *tiles, int ntiles, int cur,
                                 cudaStream_t st) {
-#if LBM_BATCH_PERSISTENT
-    if (halo) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::min(ntiles, sms * LBM_MIN_BLOCKS);
-    batch_step_kernel<QG, G_SW, H_SW, TY, TZ, 0><<<grid, dim3(TX, TY, TZ), 0, st>>>(a, tiles, cur, ntiles);
-#else
     if (halo)
         batch_step_kernel<QG, G_SW, H_SW, TY, TZ, 1><<<ntiles, dim3(TX, TY, TZ), 0, st>>>(a, tiles, cur, ntiles);
     else
         batch_step_kernel<QG, G_SW, H_SW, TY, TZ, 0><<<ntiles, dim3(TX, TY, TZ), 0, st>>>(a, tiles, cur, ntiles);
-#endif
     return cudaGetLastError();
 }
 
