@@ -130,7 +130,8 @@ def kernel_source_hash() -> str:
     blank space removed (a change of comments leaves the recorded counters
     valid)."""
     h = hashlib.sha256()
-    for f in ("lbm_step.cu", "lbm_pair.cu", "lbm_pair_impl.cuh", "lbm_step_impl.cuh", "lbm_device.cuh",
+    for f in ("lbm_step.cu", "lbm_pair.cu", "lbm_pair_launch.cuh", "lbm_pair_fp32.cu", "lbm_pair_fp16.cu",
+              "lbm_pair_bf16.cu", "lbm_pair_wide.cu", "lbm_pair_impl.cuh", "lbm_step_impl.cuh", "lbm_device.cuh",
               "lbm_internal.h"):
         with open(os.path.join(ROOT, "paper_2012_06144_gb300", "csrc", f)) as fh:
             text = fh.read()

@@ -24,8 +24,8 @@ OBJDIR = os.path.join(LIBDIR, "obj")
 LIBRARY = os.path.join(LIBDIR, "liblbm.so")
 PROBE = os.path.join(LIBDIR, "pattern_probe")  # streaming-pattern bandwidth ceiling (pattern_probe.cu)
 
-SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_pair.cu", "lbm_aux.cu", "lbm_noalloc.cu", "lbm_batch.cu",
-           "lbm_unfused.cu"]
+SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_pair.cu", "lbm_pair_fp32.cu", "lbm_pair_fp16.cu", "lbm_pair_bf16.cu",
+           "lbm_pair_wide.cu", "lbm_aux.cu", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_unfused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-I", CSRC, "-I", INCLUDE]

@@ -1,82 +1,11 @@
-// lbm_pair.cu -- the fused coupled step with two cells per thread: the
-// single-simulation kernel and its launchers.  The device code, and what the
-// form does, are in lbm_pair_impl.cuh.
-#include "lbm_pair_impl.cuh"
-
-#ifndef LBM_PAIR_MIN_BLOCKS_WIDE
-#define LBM_PAIR_MIN_BLOCKS_WIDE 3  // the same for pairs of lattices holding 46 or more populations
-#endif
-#ifndef LBM_PAIR_MIN_BLOCKS_2D
-#define LBM_PAIR_MIN_BLOCKS_2D 6  // and for the two-dimensional pair (8192 x 16384, MLUPS: 4 blocks 41,586, 5: 43,991, 6: 45,029, 7: 43,886)
-#endif
+// lbm_pair.cu -- the fused coupled step with two cells per thread: where it
+// applies and which instance runs.  The device code, and what the form does, are
+// in lbm_pair_impl.cuh; the kernel and its launch templates in lbm_pair_launch.cuh,
+// instantiated per storage format in lbm_pair_fp32.cu, lbm_pair_fp16.cu,
+// lbm_pair_bf16.cu and lbm_pair_wide.cu.
+#include "lbm_pair_launch.cuh"
 
 namespace lbm {
-namespace pairstep {
-
-template <int QG, int QP>
-constexpr int pair_min_blocks() {
-    return QP == 9 ? LBM_PAIR_MIN_BLOCKS_2D : (QG + QP >= 46 ? LBM_PAIR_MIN_BLOCKS_WIDE : LBM_PAIR_MIN_BLOCKS);
-}
-
-#ifndef LBM_PAIR_TY2D
-#define LBM_PAIR_TY2D 4
-#endif
-
-// Tile of the step: 64 x 2 x 2 cells, or 64 x LBM_PAIR_TY2D x 1 for the two-dimensional pair
-template <int QP>
-constexpr int pair_ty() { return QP == 9 ? LBM_PAIR_TY2D : TY; }
-template <int QP>
-constexpr int pair_tz() { return QP == 9 ? 1 : TZ; }
-
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool PMRT = false, bool W64 = false>
-__global__ void __launch_bounds__(TX *pair_ty<QP>() * pair_tz<QP>(), pair_min_blocks<QG, QP>())
-    pair_step_kernel(Params p, Lat<T, W64> lh, Lat<T, W64> lg, const float *__restrict__ phi_in,
-                     float *__restrict__ phi_out,
-                     int *__restrict__ flag) {
-    constexpr int TYk = pair_ty<QP>(), TZk = pair_tz<QP>();
-    __shared__ __align__(16) float tile[TZk + 2][TYk + 2][ROW];
-    // blockIdx.x runs over the (x, y) tiles, x fastest; blockIdx.y over z
-    const int nbx = (p.nx + PX - 1) / PX;
-    const int by = blockIdx.x / nbx, bx = blockIdx.x - by * nbx;
-    pair_tile<T, QG, QP, G_SW, H_SW, TX, TYk, TZk, false, PMRT>(p, lh, lg, phi_in, phi_out, flag, tile, bx, by,
-                                                                blockIdx.y);
-}
-
-template <typename T, int QG, int QP, bool G_SW, bool H_SW, bool PMRT = false, bool W64 = false>
-cudaError_t launch_pair(const Params &p, const Storage &sto, const float *pi, float *po, int *flag,
-                        cudaStream_t st) {
-    const Lat<T, W64> lh{sto.h.rest, static_cast<T *>(sto.h.mov), (unsigned)p.N};
-    const Lat<T, W64> lg{sto.g.rest, static_cast<T *>(sto.g.mov), (unsigned)p.N};
-    constexpr int TYk = pair_ty<QP>(), TZk = pair_tz<QP>();
-    const dim3 block(TX, TYk, TZk);
-    const dim3 grid(((p.nx + PX - 1) / PX) * ((p.ny + TYk - 1) / TYk), (p.nz + TZk - 1) / TZk);
-    pair_step_kernel<T, QG, QP, G_SW, H_SW, PMRT, W64><<<grid, block, 0, st>>>(p, lh, lg, pi, po, flag);
-    return cudaGetLastError();
-}
-
-template <typename T, int QP, bool PMRT = false, bool W64 = false>
-cudaError_t launch_pair_layouts(const Params &p, const Storage &sto, int q_hydro, bool g_sw, bool h_sw,
-                                const float *pi, float *po, int *flag, cudaStream_t st) {
-    if (g_sw == h_sw) return cudaErrorInvalidValue;
-    if (q_hydro == 27)
-        return g_sw ? launch_pair<T, 27, QP, true, false, PMRT, W64>(p, sto, pi, po, flag, st)
-                    : launch_pair<T, 27, QP, false, true, PMRT, W64>(p, sto, pi, po, flag, st);
-    if (q_hydro == 19)
-        return g_sw ? launch_pair<T, 19, QP, true, false, PMRT, W64>(p, sto, pi, po, flag, st)
-                    : launch_pair<T, 19, QP, false, true, PMRT, W64>(p, sto, pi, po, flag, st);
-    return cudaErrorInvalidValue;
-}
-
-// the two-dimensional pair: D2Q9 for both lattices
-template <typename T>
-cudaError_t launch_pair_2d(const Params &p, const Storage &sto, bool g_sw, bool h_sw, const float *pi, float *po,
-                           int *flag, cudaStream_t st) {
-    if (g_sw == h_sw) return cudaErrorInvalidValue;
-    return g_sw ? launch_pair<T, 9, 9, true, false>(p, sto, pi, po, flag, st)
-                : launch_pair<T, 9, 9, false, true>(p, sto, pi, po, flag, st);
-}
-
-}  // namespace pairstep
 
 bool pair_step_applies(const Params &p, int q_hydro, int q_phase, int precision) {
     if (p.step_form == LBM_FORM_FUSED_CELL) return false;
@@ -98,29 +27,15 @@ cudaError_t launch_pair_step(const Params &p, const Storage &sto, int q_hydro, i
                              const float *phi_in, float *phi_out, int *flag, cudaStream_t st) {
     if (q_phase != 15) {
         if (sto.precision != LBM_PRECISION_FP32) return cudaErrorInvalidValue;
-        if (q_phase == 9) return pairstep::launch_pair_2d<float>(p, sto, g_sw, h_sw, phi_in, phi_out, flag, st);
-        if (q_phase == 19)
-            return pairstep::launch_pair_layouts<float, 19>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
-        if (q_phase == 27)
-            return pairstep::launch_pair_layouts<float, 27>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
-        return cudaErrorInvalidValue;
+        return pairstep::launch_pair_wide(p, sto, q_hydro, q_phase, g_sw, h_sw, phi_in, phi_out, flag, st);
     }
     switch (sto.precision) {
         case LBM_PRECISION_FP32:
-            if (!offsets32(p.N, q_hydro, q_phase))
-                return p.phase_mrt ? pairstep::launch_pair_layouts<float, 15, true, true>(p, sto, q_hydro, g_sw, h_sw,
-                                                                                         phi_in, phi_out, flag, st)
-                                   : pairstep::launch_pair_layouts<float, 15, false, true>(p, sto, q_hydro, g_sw, h_sw,
-                                                                                          phi_in, phi_out, flag, st);
-            if (p.phase_mrt)
-                return pairstep::launch_pair_layouts<float, 15, true>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out,
-                                                                      flag, st);
-            return pairstep::launch_pair_layouts<float, 15>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
+            return pairstep::launch_pair_fp32(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
         case LBM_PRECISION_FP16:
-            return pairstep::launch_pair_layouts<__half, 15>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
+            return pairstep::launch_pair_fp16(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
         case LBM_PRECISION_BF16:
-            return pairstep::launch_pair_layouts<__nv_bfloat16, 15>(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out,
-                                                                    flag, st);
+            return pairstep::launch_pair_bf16(p, sto, q_hydro, g_sw, h_sw, phi_in, phi_out, flag, st);
         default:
             return cudaErrorInvalidValue;
     }
